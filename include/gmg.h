@@ -1,0 +1,168 @@
+/*
+ * gmg.h -- C ABI of the GB300 multiplicative vertex-patch smoother and the
+ * geometric multigrid / conjugate-gradient solver built around it.
+ *
+ * Method: Wichrowski, Munch, Kronbichler, Kanschat, "Smoothers with localized
+ * residual computations for geometric multigrid methods" (arXiv 2407.02100).
+ *
+ * Problem: -div(grad u) = f on the unit square/cube, homogeneous Dirichlet
+ * data, continuous Q_k elements (Gauss-Lobatto support points) on a uniform
+ * Cartesian mesh of n cells per direction (App. A.2), with nested levels
+ * obtained by halving n (Sec. 2).
+ *
+ * VECTOR LAYOUT (every vector argument).  A level with n cells has
+ * N = n k + 1 nodes per direction.  Node (i_0, i_1[, i_2]) is stored at
+ *     i_0 + pitch_y * i_1 [+ pitch_z * i_2],
+ * with pitch_y = N rounded up to a multiple of 4 and pitch_z = pitch_y * N;
+ * a vector holds n_elems = pitch_y * N (2D) or pitch_z * N (3D) elements.
+ * gmg_vector_layout() returns these numbers.  Dirichlet nodes (any index 0
+ * or N-1) and padding entries (i_0 >= N) must be zero on input; every call
+ * keeps them zero.  Vectors are DEVICE pointers owned by the caller, of the
+ * element type given per call (double, or float for GMG_FP32 level vectors).
+ *
+ * STREAMS.  Every call is enqueued on gmg_desc.stream (a cudaStream_t; NULL
+ * = legacy default stream) and returns without waiting, except
+ * cg_gmg_solve(), which synchronises the stream to read back scalars.
+ *
+ * ERRORS.  Every entry point returns GMG_OK (0) or a negative status; no
+ * C++ exception crosses the ABI.  gmg_status_string() names a status.
+ * A problem object must not be used from two host threads at once.
+ */
+#ifndef GMG_H
+#define GMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum gmg_status {
+  GMG_OK = 0,
+  GMG_ERR_INVALID_ARG = -1,   /* bad descriptor, level, pointer or size */
+  GMG_ERR_OOM = -2,           /* device allocation failed */
+  GMG_ERR_CUDA = -3,          /* a CUDA runtime call or launch failed */
+  GMG_ERR_NONFINITE = -4,     /* NaN/Inf met in a solver scalar */
+  GMG_ERR_BREAKDOWN = -5,     /* CG breakdown: p^T A p <= 0 or r^T z <= 0 */
+  GMG_ERR_NOT_CONVERGED = -6, /* max_it reached above the tolerance */
+  GMG_ERR_UNSUPPORTED = -7    /* valid but not implemented combination */
+};
+
+enum gmg_precision {
+  GMG_FP64 = 0,  /* smoother, transfer and V-cycle in double */
+  GMG_FP32 = 1   /* smoother, transfer and V-cycle in float (inside FP64 CG) */
+};
+
+typedef struct gmg_problem gmg_problem; /* opaque; owns all level data */
+
+typedef struct {
+  int dim;          /* 2 or 3 */
+  int degree;       /* k, 1..8 */
+  int n_cells;      /* cells per direction on the finest level, >= 2 */
+  int n_levels;     /* >= 1; 0 = halve n while it stays even and >= 2 */
+  int precision;    /* enum gmg_precision */
+  double damping;   /* omega of the scatter u += omega d (1.0 = the paper's P_j) */
+  int pre_sweeps;   /* smoothing steps before the coarse correction (>= 0) */
+  int post_sweeps;  /* smoothing steps after it (>= 0) */
+  void* stream;     /* cudaStream_t used by every call on this problem */
+} gmg_desc;
+
+typedef struct {
+  int iterations;            /* CG iterations done */
+  int converged;             /* 1 if ||r|| <= rtol ||b|| */
+  double initial_residual;   /* ||b - A u_0|| */
+  double final_residual;     /* ||b - A u|| (recurrence residual) */
+  double relative_residual;  /* final_residual / ||b|| */
+  double residual_history[64]; /* relative residuals, entry i after iteration i */
+} gmg_solve_stats;
+
+/* Create a problem: builds the level hierarchy (Sec. 2, nested meshes), the
+ * 1D reference matrices, the fast-diagonalisation data of the patch (App.
+ * A.3, K T = M T Lambda with T^T M T = I) and of the coarsest level, and
+ * allocates the internal level vectors on the current CUDA device.
+ * desc: read only; *out receives the new problem (NULL on failure).
+ * Errors: INVALID_ARG (dim not 2/3, degree not 1..8, n_cells < 2, levels
+ * not possible for n_cells, precision unknown, damping not finite), OOM,
+ * CUDA. */
+int gmg_create(const gmg_desc* desc, gmg_problem** out);
+
+/* Release every device buffer of the problem after synchronising its
+ * stream.  NULL is accepted. */
+int gmg_destroy(gmg_problem* p);
+
+/* Layout of vectors on `level` (0 = coarsest, n_levels-1 = finest); see the
+ * layout note above.  Any output pointer may be NULL.  Host-only. */
+int gmg_vector_layout(const gmg_problem* p, int level, long long* n_elems,
+                      int* nodes_1d, int* pitch_y, long long* pitch_z);
+
+/* Number of levels and cells per direction of a level.  Host-only. */
+int gmg_level_info(const gmg_problem* p, int level, int* n_cells, int* n_levels);
+
+/* y = A_level x: the matrix-free stiffness operator of the level (Sec. 2,
+ * eq. "matrix"; evaluated by sum factorisation of the tensor-product cell
+ * operators, App. A.1).  x, y: device vectors of the problem's level-vector
+ * type (double for GMG_FP64, float for GMG_FP32), distinct buffers.
+ * Dirichlet rows of y are written as zero. */
+int gmg_apply_operator(gmg_problem* p, int level, const void* x, void* y);
+
+/* Same operator in double precision regardless of the problem precision
+ * (the operator used by the outer CG).  Finest level only is guaranteed to
+ * be allocated for GMG_FP32 problems; any level for GMG_FP64. */
+int gmg_apply_operator_f64(gmg_problem* p, int level, const double* x, double* y);
+
+/* Multiplicative vertex-patch smoothing on `level`, in place on u, with
+ * right-hand side b: n_sweeps steps of the combined colourised smoother
+ * (Algorithm 4).  Each patch gathers u on its closure and b on its interior
+ * (eq. "gather"), forms the local residual r_j = b_j - Pi_j bar A_j bar u_j
+ * (eq. "main:4"), solves A_j d_j = r_j by fast diagonalisation (App. A.3,
+ * eq. "fdm:inverse"), and adds omega d_j to the patch interior (eq.
+ * "scatter").  Colours c = sum_a 2^a (v_a mod 2) of the vertex v are taken
+ * in ascending order, or descending when reverse != 0.  u, b: level vectors
+ * of the problem's type. */
+int gmg_smooth(gmg_problem* p, int level, void* u, const void* b, int n_sweeps, int reverse);
+
+/* One colour of the smoother (all patches of colour `colour`, 0..2^dim-1),
+ * in place on u.  Same arguments and semantics as gmg_smooth. */
+int gmg_smooth_colour(gmg_problem* p, int level, void* u, const void* b, int colour);
+
+/* coarse = R fine with R = P^T, the transpose of the embedding prolongation
+ * (Sec. 2, restriction as the adjoint of the embedding).  fine: level
+ * `fine_level` (>= 1), coarse: level fine_level-1; problem's vector type. */
+int gmg_restrict(gmg_problem* p, int fine_level, const void* fine, void* coarse);
+
+/* fine += P coarse, P the embedding of V_{l} into V_{l+1} (Sec. 2).
+ * coarse: level `coarse_level`, fine: level coarse_level+1. */
+int gmg_prolongate_add(gmg_problem* p, int coarse_level, const void* coarse, void* fine);
+
+/* x = A_0^{-1} b on the coarsest level, by fast diagonalisation of the
+ * whole level (exact for the constant-coefficient Cartesian operator). */
+int gmg_coarse_solve(gmg_problem* p, const void* b, void* x);
+
+/* x = V(b): one V-cycle on the finest level with x_0 = 0 (Sec. 2, the
+ * V-cycle; pre-smoothing with ascending colours, post-smoothing with
+ * descending colours, exact coarse solve).  x, b: finest-level vectors of
+ * the problem's type. */
+int gmg_vcycle(gmg_problem* p, void* x, const void* b);
+
+/* Preconditioned CG on the finest level in double precision, preconditioned
+ * by one V-cycle per iteration (in the problem's precision).  u: initial
+ * guess on input (a restart resumes from it), solution on output; b: right
+ * hand side; both double device vectors.  Stops when ||r|| <= rtol ||b||.
+ * stats may be NULL.  Errors: INVALID_ARG, CUDA, NONFINITE, BREAKDOWN,
+ * NOT_CONVERGED (u then holds the last iterate). */
+int cg_gmg_solve(gmg_problem* p, double* u, const double* b, double rtol, int max_it,
+                 gmg_solve_stats* stats);
+
+/* Host-only set-up math exposed for testing: the 1D fast-diagonalisation
+ * data of one vertex patch built from two cells of unit width (App. A.3):
+ * M, K = interior (2k-1)x(2k-1) mass and stiffness of the two-cell 1D
+ * Q_k mesh, T with T^T M T = I and T^T K T = diag(lambda).  All arrays are
+ * row-major, caller-allocated, of (2k-1)^2 (M, K, T) and 2k-1 (lambda)
+ * doubles; any may be NULL. */
+int gmg_patch_fd_1d(int degree, double* M, double* K, double* T, double* lambda);
+
+/* Human-readable name of a status code (static storage). */
+const char* gmg_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GMG_H */

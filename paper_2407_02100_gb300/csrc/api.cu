@@ -1,0 +1,632 @@
+// C ABI (include/gmg.h): problem set-up, level operations, V-cycle and the
+// preconditioned conjugate gradient driver.  All numerical work runs in the
+// CUDA kernels of patch_f64.cu / patch_f32.cu / vector_kernels.cu; this file
+// only builds tables on the host, owns device buffers and sequences launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/gmg.h"
+#include "kernels.h"
+#include "setup.h"
+
+using namespace gmg;
+
+namespace {
+
+struct Level {
+  LevelGeom g;
+  long long n_elems = 0;
+  double h = 0.0;
+  void* u = nullptr;  // level correction (problem precision)
+  void* b = nullptr;  // level right-hand side (problem precision)
+  void* r = nullptr;  // level residual (problem precision)
+};
+
+}  // namespace
+
+struct gmg_problem {
+  gmg_desc desc{};
+  cudaStream_t stream = nullptr;
+  size_t esize = 8;  // bytes per level-vector element
+  std::vector<Level> levels;
+  // patch fast diagonalisation: 1/(sum of eigenvalues) over M^d modes
+  void* dinv = nullptr;
+  // transfer tables (problem precision): prolongation 2k x (k+1),
+  // restriction k x (4k-1)
+  void* coef_prol = nullptr;
+  void* coef_rest = nullptr;
+  void* tmp1 = nullptr;  // transfer temporaries
+  void* tmp2 = nullptr;
+  // coarsest-level fast diagonalisation
+  int m0 = 0;
+  void* coef_c_fwd = nullptr;  // T0^T  (m0 x m0)
+  void* coef_c_bwd = nullptr;  // T0    (m0 x m0)
+  void* dinv0 = nullptr;       // h0^{2-d} / sum lambda
+  void* ctmp1 = nullptr;
+  void* ctmp2 = nullptr;
+  // outer CG (double, finest level)
+  double* cg_r = nullptr;
+  double* cg_z = nullptr;
+  double* cg_p = nullptr;
+  double* cg_q = nullptr;
+  double* partial = nullptr;
+  double* scal = nullptr;  // device scalars, see enum below
+  std::vector<void*> owned;
+};
+
+namespace {
+
+enum { S_RZ = 0, S_PQ = 1, S_RR = 2, S_RZN = 3, S_BB = 4, S_COUNT = 8 };
+
+int dalloc(gmg_problem* p, void** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return GMG_ERR_OOM;
+  }
+  p->owned.push_back(*ptr);
+  if (cudaMemset(*ptr, 0, bytes) != cudaSuccess) return GMG_ERR_CUDA;
+  return GMG_OK;
+}
+
+// upload host doubles as the problem precision
+int upload_table(gmg_problem* p, void** dst, const std::vector<double>& src) {
+  int st = dalloc(p, dst, src.size() * p->esize);
+  if (st) return st;
+  cudaError_t e;
+  if (p->esize == 8) {
+    e = cudaMemcpy(*dst, src.data(), src.size() * 8, cudaMemcpyHostToDevice);
+  } else {
+    std::vector<float> f(src.begin(), src.end());
+    e = cudaMemcpy(*dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice);
+  }
+  return e == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+}
+
+LevelGeom make_geom(int dim, int k, int n) {
+  LevelGeom g;
+  g.dim = dim;
+  g.k = k;
+  g.n = n;
+  g.N = n * k + 1;
+  g.py = (g.N + 3) / 4 * 4;
+  g.pz = (long long)g.py * g.N;
+  return g;
+}
+
+long long geom_elems(const LevelGeom& g) { return g.dim == 3 ? g.pz * g.N : (long long)g.py * g.N; }
+
+bool valid_level(const gmg_problem* p, int level) {
+  return p && level >= 0 && level < (int)p->levels.size();
+}
+
+#define CHECK(x)                 \
+  do {                           \
+    int st_ = (x);               \
+    if (st_ != GMG_OK) return st_; \
+  } while (0)
+
+// ---- typed dispatch helpers ----
+int apply_level(gmg_problem* p, int level, const void* x, void* y, const void* bvec, double alpha,
+                double beta) {
+  const Level& L = p->levels[level];
+  ApplyLaunch al;
+  al.g = L.g;
+  al.alpha = alpha;
+  al.beta = beta;
+  if (p->esize == 8)
+    return launch_apply<double>(al, (const double*)x, (double*)y, (const double*)bvec, p->stream);
+  return launch_apply<float>(al, (const float*)x, (float*)y, (const float*)bvec, p->stream);
+}
+
+double op_scale(const Level& L) { return L.g.dim == 3 ? L.h : 1.0; }  // h^{d-2}
+
+int smooth_colour(gmg_problem* p, int level, void* u, const void* b, int colour) {
+  const Level& L = p->levels[level];
+  const int dim = L.g.dim, n = L.g.n;
+  PatchLaunch pl;
+  pl.g = L.g;
+  pl.n_patches = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (a < dim) {
+      bool odd = (colour >> a) & 1;
+      pl.first[a] = odd ? 1 : 2;
+      pl.count[a] = odd ? n / 2 : (n - 1) / 2;
+    } else {
+      pl.first[a] = 1;
+      pl.count[a] = 1;
+    }
+    pl.n_patches *= pl.count[a];
+  }
+  pl.sb = dim == 3 ? 1.0 / L.h : 1.0;
+  pl.omega = p->desc.damping;
+  if (pl.n_patches == 0) return GMG_OK;
+  if (p->esize == 8)
+    return launch_patch_colour<double>(pl, (double*)u, (const double*)b, (const double*)p->dinv, p->stream);
+  return launch_patch_colour<float>(pl, (float*)u, (const float*)b, (const float*)p->dinv, p->stream);
+}
+
+int smooth(gmg_problem* p, int level, void* u, const void* b, int n_sweeps, int reverse) {
+  const int nc = 1 << p->levels[level].g.dim;
+  for (int s = 0; s < n_sweeps; ++s)
+    for (int i = 0; i < nc; ++i) CHECK(smooth_colour(p, level, u, b, reverse ? nc - 1 - i : i));
+  return GMG_OK;
+}
+
+int axis_op(gmg_problem* p, const AxisOp& op, const void* in, void* out, const void* coef) {
+  if (p->esize == 8) return launch_axis_op<double>(op, (const double*)in, (double*)out, (const double*)coef, p->stream);
+  return launch_axis_op<float>(op, (const float*)in, (float*)out, (const float*)coef, p->stream);
+}
+
+// Describe a dense array of extents e[3] (x fastest) with given strides.
+struct Arr {
+  int e[3];
+  long long s[3];
+};
+Arr level_arr(const LevelGeom& g) {
+  Arr a;
+  a.e[0] = g.N; a.e[1] = g.N; a.e[2] = g.dim == 3 ? g.N : 1;
+  a.s[0] = 1; a.s[1] = g.py; a.s[2] = g.dim == 3 ? g.pz : 0;
+  return a;
+}
+Arr compact_arr(int e0, int e1, int e2) {
+  Arr a;
+  a.e[0] = e0; a.e[1] = e1; a.e[2] = e2;
+  a.s[0] = 1; a.s[1] = e0; a.s[2] = (long long)e0 * e1;
+  return a;
+}
+
+// One pass along `axis`: computes cnt[] outputs at out_off[] from `in`.
+AxisOp make_op(int axis, const Arr& in, const int in_off[3], const Arr& out, const int cnt[3],
+               const int out_off[3], int R, int S, int off, int W, int acc) {
+  AxisOp op;
+  op.axis = axis;
+  for (int a = 0; a < 3; ++a) {
+    op.cnt[a] = cnt[a];
+    op.in_dim[a] = in.e[a];
+    op.in_stride[a] = in.s[a];
+    op.in_off[a] = in_off[a];
+    op.out_stride[a] = out.s[a];
+    op.out_off[a] = out_off[a];
+  }
+  op.R = R; op.S = S; op.off = off; op.W = W;
+  op.shift = 0;
+  op.accumulate = acc;
+  return op;
+}
+
+// fine += P coarse (tensor product of the 1D embedding, one axis per pass)
+int prolongate_add(gmg_problem* p, int cl, const void* coarse, void* fine) {
+  const LevelGeom& gc = p->levels[cl].g;
+  const LevelGeom& gf = p->levels[cl + 1].g;
+  const int k = gc.k, dim = gc.dim, Nc = gc.N, Nf = gf.N;
+  const int zero[3] = {0, 0, 0};
+  Arr cur = level_arr(gc);
+  const void* src = coarse;
+  int ext[3] = {Nc, Nc, dim == 3 ? Nc : 1};
+  for (int a = 0; a < dim; ++a) {
+    ext[a] = Nf;
+    const bool last = (a == dim - 1);
+    Arr out = last ? level_arr(gf) : compact_arr(ext[0], ext[1], ext[2]);
+    void* dst = last ? fine : (a % 2 == 0 ? p->tmp1 : p->tmp2);
+    AxisOp op = make_op(a, cur, zero, out, ext, zero, 2 * k, k, 0, k + 1, last ? 1 : 0);
+    CHECK(axis_op(p, op, src, dst, p->coef_prol));
+    cur = out;
+    src = dst;
+  }
+  return GMG_OK;
+}
+
+// coarse = P^T fine on the interior coarse nodes (Dirichlet ones stay zero):
+// one axis per pass; along axes already restricted only interior coarse
+// nodes are computed, stored at their lattice index.
+int restrict_to(gmg_problem* p, int fl, const void* fine, void* coarse) {
+  const LevelGeom& gf = p->levels[fl].g;
+  const LevelGeom& gc = p->levels[fl - 1].g;
+  const int k = gc.k, dim = gc.dim, Nc = gc.N, Nf = gf.N;
+  Arr cur = level_arr(gf);
+  const void* src = fine;
+  int ext[3] = {Nf, Nf, dim == 3 ? Nf : 1};
+  for (int a = 0; a < dim; ++a) {
+    int store[3] = {ext[0], ext[1], ext[2]};
+    store[a] = Nc;
+    int cnt[3], ooff[3], ioff[3];
+    for (int b2 = 0; b2 < 3; ++b2) {
+      const bool restricted = b2 < dim && b2 <= a;
+      cnt[b2] = restricted ? Nc - 2 : store[b2];
+      ooff[b2] = restricted ? 1 : 0;
+      ioff[b2] = (b2 < dim && b2 < a) ? 1 : 0;
+    }
+    const bool last = (a == dim - 1);
+    Arr out = last ? level_arr(gc) : compact_arr(store[0], store[1], store[2]);
+    void* dst = last ? coarse : (a % 2 == 0 ? p->tmp1 : p->tmp2);
+    // coarse node c = o + 1 gathers fine nodes 2k(c/k) - (2k-1) .. + (2k-1)
+    AxisOp op = make_op(a, cur, ioff, out, cnt, ooff, k, 2 * k, -(2 * k - 1), 4 * k - 1, 0);
+    op.shift = 1;
+    CHECK(axis_op(p, op, src, dst, p->coef_rest));
+    cur = out;
+    src = dst;
+    ext[a] = Nc;
+  }
+  return GMG_OK;
+}
+
+int coarse_solve(gmg_problem* p, const void* b, void* x) {
+  const LevelGeom& g = p->levels[0].g;
+  const int dim = g.dim, m = p->m0;
+  const int zero[3] = {0, 0, 0};
+  const int one[3] = {1, 1, dim == 3 ? 1 : 0};
+  int cnt[3] = {m, m, dim == 3 ? m : 1};
+  Arr lev = level_arr(g);
+  Arr cmp = compact_arr(m, m, dim == 3 ? m : 1);
+  // forward: t = (T^T x .. x T^T) b on the interior
+  const void* src = b;
+  Arr cur = lev;
+  for (int a = 0; a < dim; ++a) {
+    const bool first = (a == 0);
+    void* dst = (a % 2 == 0) ? p->ctmp1 : p->ctmp2;
+    int in_off[3];
+    for (int b2 = 0; b2 < 3; ++b2) in_off[b2] = first ? one[b2] : 0;
+    AxisOp op = make_op(a, cur, in_off, cmp, cnt, zero, m, 0, first ? 1 : 0, m, 0);
+    CHECK(axis_op(p, op, src, dst, p->coef_c_fwd));
+    cur = cmp;
+    src = dst;
+  }
+  long long nm = (long long)m * m * (dim == 3 ? m : 1);
+  if (p->esize == 8) CHECK(launch_scale<double>(nm, (double*)src, (const double*)p->dinv0, p->stream));
+  else CHECK(launch_scale<float>(nm, (float*)src, (const float*)p->dinv0, p->stream));
+  // backward: x = (T x .. x T) t into the level interior
+  for (int a = 0; a < dim; ++a) {
+    const bool last = (a == dim - 1);
+    void* dst = last ? x : (src == p->ctmp1 ? p->ctmp2 : p->ctmp1);
+    Arr out = last ? lev : cmp;
+    const int* ooff = last ? one : zero;
+    AxisOp op = make_op(a, cur, zero, out, cnt, ooff, m, 0, 0, m, 0);
+    CHECK(axis_op(p, op, src, dst, p->coef_c_bwd));
+    src = dst;
+  }
+  return GMG_OK;
+}
+
+int vcycle_level(gmg_problem* p, int l, void* x, const void* b) {
+  Level& L = p->levels[l];
+  if (l == 0) return coarse_solve(p, b, x);
+  if (cudaMemsetAsync(x, 0, L.n_elems * p->esize, p->stream) != cudaSuccess) return GMG_ERR_CUDA;
+  CHECK(smooth(p, l, x, b, p->desc.pre_sweeps, 0));
+  CHECK(apply_level(p, l, x, L.r, b, -op_scale(L), 1.0));
+  Level& C = p->levels[l - 1];
+  CHECK(restrict_to(p, l, L.r, C.b));
+  CHECK(vcycle_level(p, l - 1, C.u, C.b));
+  CHECK(prolongate_add(p, l - 1, C.u, x));
+  CHECK(smooth(p, l, x, b, p->desc.post_sweeps, 1));
+  return GMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gmg_status_string(int s) {
+  switch (s) {
+    case GMG_OK: return "ok";
+    case GMG_ERR_INVALID_ARG: return "invalid argument";
+    case GMG_ERR_OOM: return "device out of memory";
+    case GMG_ERR_CUDA: return "CUDA error";
+    case GMG_ERR_NONFINITE: return "non-finite value in solver";
+    case GMG_ERR_BREAKDOWN: return "CG breakdown";
+    case GMG_ERR_NOT_CONVERGED: return "not converged";
+    case GMG_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+int gmg_patch_fd_1d(int k, double* M, double* K, double* T, double* lambda) {
+  if (k < 1 || k > kMaxDegree) return GMG_ERR_INVALID_ARG;
+  const int m = 2 * k - 1;
+  std::vector<double> Mi, Ki, Ti, li;
+  assembled_1d(k, 2, 1, m, 1, m, Mi, Ki);
+  if (!generalized_eigen(m, Mi, Ki, Ti, li)) return GMG_ERR_INVALID_ARG;
+  if (M) std::memcpy(M, Mi.data(), sizeof(double) * m * m);
+  if (K) std::memcpy(K, Ki.data(), sizeof(double) * m * m);
+  if (T) std::memcpy(T, Ti.data(), sizeof(double) * m * m);
+  if (lambda) std::memcpy(lambda, li.data(), sizeof(double) * m);
+  return GMG_OK;
+}
+
+int gmg_destroy(gmg_problem* p) {
+  if (!p) return GMG_OK;
+  cudaStreamSynchronize(p->stream);
+  for (void* ptr : p->owned) cudaFree(ptr);
+  delete p;
+  return GMG_OK;
+}
+
+static int create_impl(const gmg_desc* d, gmg_problem* p) {
+  p->desc = *d;
+  p->stream = (cudaStream_t)d->stream;
+  p->esize = d->precision == GMG_FP32 ? 4 : 8;
+  const int dim = d->dim, k = d->degree;
+  // level hierarchy: n_levels given, or halve while even and >= 2
+  int L = d->n_levels;
+  if (L == 0) {
+    L = 1;
+    int n = d->n_cells;
+    while (n % 2 == 0 && n / 2 >= 2) { n /= 2; ++L; }
+  }
+  for (int l = 0; l < L; ++l) {
+    int shift = L - 1 - l;
+    int n = d->n_cells >> shift;
+    if (n < 1 || (n << shift) != d->n_cells) return GMG_ERR_INVALID_ARG;
+    if (l > 0 && n < 2) return GMG_ERR_INVALID_ARG;
+  }
+  if ((d->n_cells >> (L - 1)) < 1) return GMG_ERR_INVALID_ARG;
+  p->levels.resize(L);
+  for (int l = 0; l < L; ++l) {
+    Level& lv = p->levels[l];
+    int n = d->n_cells >> (L - 1 - l);
+    lv.g = make_geom(dim, k, n);
+    lv.n_elems = geom_elems(lv.g);
+    lv.h = 1.0 / n;
+    CHECK(dalloc(p, &lv.u, lv.n_elems * p->esize));
+    CHECK(dalloc(p, &lv.b, lv.n_elems * p->esize));
+    CHECK(dalloc(p, &lv.r, lv.n_elems * p->esize));
+  }
+  // 1D tables: unit cell, two-cell patch (interior rows x closure cols), FD
+  const int m = 2 * k - 1, C = 2 * k + 1;
+  std::vector<double> Mc, Kc, Mp, Kp, Mi, Ki, Tp, lp;
+  cell_matrices_1d(k, Mc, Kc);
+  assembled_1d(k, 2, 1, m, 0, C, Mp, Kp);
+  assembled_1d(k, 2, 1, m, 1, m, Mi, Ki);
+  if (!generalized_eigen(m, Mi, Ki, Tp, lp)) return GMG_ERR_INVALID_ARG;
+  CHECK(upload_patch_tables<double>(k, Mp.data(), Kp.data(), Tp.data(), Mc.data(), Kc.data(), p->stream));
+  CHECK(upload_patch_tables<float>(k, Mp.data(), Kp.data(), Tp.data(), Mc.data(), Kc.data(), p->stream));
+  const int nint = dim == 3 ? m * m * m : m * m;
+  std::vector<double> dinv(nint);
+  for (int t = 0; t < nint; ++t) {
+    int x = t % m, y = (t / m) % m, z = t / (m * m);
+    double s = lp[x] + lp[y] + (dim == 3 ? lp[z] : 0.0);
+    dinv[t] = 1.0 / s;
+  }
+  CHECK(upload_table(p, &p->dinv, dinv));
+  // transfer tables
+  std::vector<double> P1;
+  prolongation_cell_1d(k, P1);  // (2k+1) x (k+1)
+  std::vector<double> prol(2 * k * (k + 1));
+  for (int r = 0; r < 2 * k; ++r)
+    for (int q = 0; q <= k; ++q) prol[r * (k + 1) + q] = P1[r * (k + 1) + q];
+  CHECK(upload_table(p, &p->coef_prol, prol));
+  const int W = 4 * k - 1;
+  std::vector<double> rest(k * W, 0.0);
+  for (int q = 0; q < k; ++q)
+    for (int w = 0; w < W; ++w) {
+      int dd = w - (2 * k - 1);  // fine offset from 2 k cc
+      double v = 0.0;
+      if (q == 0) {
+        if (dd < 0) v = P1[(2 * k + dd) * (k + 1) + k];
+        else if (dd == 0) v = 1.0;
+        else v = P1[dd * (k + 1) + 0];
+      } else if (dd >= 1 && dd <= 2 * k - 1) {
+        v = P1[dd * (k + 1) + q];
+      }
+      rest[q * W + w] = v;
+    }
+  CHECK(upload_table(p, &p->coef_rest, rest));
+  // transfer temporaries: largest intermediate array of any pass
+  long long tmax = 1;
+  for (int l = 1; l < L; ++l) {
+    long long Nf = p->levels[l].g.N, Nc = p->levels[l - 1].g.N;
+    long long t = dim == 3 ? Nf * Nf * Nc : Nf * Nc;
+    if (t > tmax) tmax = t;
+  }
+  CHECK(dalloc(p, &p->tmp1, tmax * p->esize));
+  CHECK(dalloc(p, &p->tmp2, tmax * p->esize));
+  // coarsest level: global fast diagonalisation
+  const LevelGeom& g0 = p->levels[0].g;
+  const int m0 = g0.n * k - 1;
+  p->m0 = m0;
+  if (m0 < 1) return GMG_ERR_INVALID_ARG;
+  std::vector<double> M0, K0, T0, l0;
+  assembled_1d(k, g0.n, 1, m0, 1, m0, M0, K0);
+  if (!generalized_eigen(m0, M0, K0, T0, l0)) return GMG_ERR_INVALID_ARG;
+  std::vector<double> fwd(m0 * m0), bwd(m0 * m0);
+  for (int i = 0; i < m0; ++i)
+    for (int j = 0; j < m0; ++j) {
+      fwd[i * m0 + j] = T0[j * m0 + i];
+      bwd[i * m0 + j] = T0[i * m0 + j];
+    }
+  CHECK(upload_table(p, &p->coef_c_fwd, fwd));
+  CHECK(upload_table(p, &p->coef_c_bwd, bwd));
+  const long long nm0 = (long long)m0 * m0 * (dim == 3 ? m0 : 1);
+  std::vector<double> d0(nm0);
+  const double s0 = dim == 3 ? (double)g0.n : 1.0;  // h0^{2-d}
+  for (long long t = 0; t < nm0; ++t) {
+    int x = t % m0, y = (t / m0) % m0, z = (int)(t / ((long long)m0 * m0));
+    d0[t] = s0 / (l0[x] + l0[y] + (dim == 3 ? l0[z] : 0.0));
+  }
+  CHECK(upload_table(p, &p->dinv0, d0));
+  CHECK(dalloc(p, &p->ctmp1, nm0 * p->esize));
+  CHECK(dalloc(p, &p->ctmp2, nm0 * p->esize));
+  // outer CG
+  const long long nf = p->levels[L - 1].n_elems;
+  CHECK(dalloc(p, (void**)&p->cg_r, nf * 8));
+  CHECK(dalloc(p, (void**)&p->cg_z, nf * 8));
+  CHECK(dalloc(p, (void**)&p->cg_p, nf * 8));
+  CHECK(dalloc(p, (void**)&p->cg_q, nf * 8));
+  CHECK(dalloc(p, (void**)&p->partial, kReduceBlocks * 8));
+  CHECK(dalloc(p, (void**)&p->scal, S_COUNT * 8));
+  return cudaDeviceSynchronize() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+}
+
+int gmg_create(const gmg_desc* d, gmg_problem** out) {
+  if (!out) return GMG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!d) return GMG_ERR_INVALID_ARG;
+  if (d->dim != 2 && d->dim != 3) return GMG_ERR_INVALID_ARG;
+  if (d->degree < 1 || d->degree > kMaxDegree) return GMG_ERR_INVALID_ARG;
+  if (d->n_cells < 2 || d->n_levels < 0 || d->n_levels > 30) return GMG_ERR_INVALID_ARG;
+  if (d->precision != GMG_FP64 && d->precision != GMG_FP32) return GMG_ERR_INVALID_ARG;
+  if (!std::isfinite(d->damping) || d->pre_sweeps < 0 || d->post_sweeps < 0) return GMG_ERR_INVALID_ARG;
+  // node counts must fit 32-bit lattice indices
+  if ((long long)d->n_cells * d->degree + 1 > (1 << 20)) return GMG_ERR_INVALID_ARG;
+  gmg_problem* p = new (std::nothrow) gmg_problem();
+  if (!p) return GMG_ERR_OOM;
+  int st = create_impl(d, p);
+  if (st != GMG_OK) {
+    gmg_destroy(p);
+    return st;
+  }
+  *out = p;
+  return GMG_OK;
+}
+
+int gmg_vector_layout(const gmg_problem* p, int level, long long* n_elems, int* nodes_1d,
+                      int* pitch_y, long long* pitch_z) {
+  if (!valid_level(p, level)) return GMG_ERR_INVALID_ARG;
+  const Level& L = p->levels[level];
+  if (n_elems) *n_elems = L.n_elems;
+  if (nodes_1d) *nodes_1d = L.g.N;
+  if (pitch_y) *pitch_y = L.g.py;
+  if (pitch_z) *pitch_z = L.g.dim == 3 ? L.g.pz : 0;
+  return GMG_OK;
+}
+
+int gmg_level_info(const gmg_problem* p, int level, int* n_cells, int* n_levels) {
+  if (!valid_level(p, level)) return GMG_ERR_INVALID_ARG;
+  if (n_cells) *n_cells = p->levels[level].g.n;
+  if (n_levels) *n_levels = (int)p->levels.size();
+  return GMG_OK;
+}
+
+int gmg_apply_operator(gmg_problem* p, int level, const void* x, void* y) {
+  if (!valid_level(p, level) || !x || !y || x == y) return GMG_ERR_INVALID_ARG;
+  return apply_level(p, level, x, y, nullptr, op_scale(p->levels[level]), 0.0);
+}
+
+int gmg_apply_operator_f64(gmg_problem* p, int level, const double* x, double* y) {
+  if (!valid_level(p, level) || !x || !y || x == y) return GMG_ERR_INVALID_ARG;
+  const Level& L = p->levels[level];
+  ApplyLaunch al;
+  al.g = L.g;
+  al.alpha = op_scale(L);
+  al.beta = 0.0;
+  return launch_apply<double>(al, x, y, nullptr, p->stream);
+}
+
+int gmg_smooth(gmg_problem* p, int level, void* u, const void* b, int n_sweeps, int reverse) {
+  if (!valid_level(p, level) || !u || !b || u == b || n_sweeps < 0) return GMG_ERR_INVALID_ARG;
+  return smooth(p, level, u, b, n_sweeps, reverse);
+}
+
+int gmg_smooth_colour(gmg_problem* p, int level, void* u, const void* b, int colour) {
+  if (!valid_level(p, level) || !u || !b || u == b) return GMG_ERR_INVALID_ARG;
+  if (colour < 0 || colour >= (1 << p->levels[level].g.dim)) return GMG_ERR_INVALID_ARG;
+  return smooth_colour(p, level, u, b, colour);
+}
+
+int gmg_restrict(gmg_problem* p, int fine_level, const void* fine, void* coarse) {
+  if (!p || fine_level < 1 || fine_level >= (int)p->levels.size() || !fine || !coarse)
+    return GMG_ERR_INVALID_ARG;
+  return restrict_to(p, fine_level, fine, coarse);
+}
+
+int gmg_prolongate_add(gmg_problem* p, int coarse_level, const void* coarse, void* fine) {
+  if (!p || coarse_level < 0 || coarse_level + 1 >= (int)p->levels.size() || !fine || !coarse)
+    return GMG_ERR_INVALID_ARG;
+  return prolongate_add(p, coarse_level, coarse, fine);
+}
+
+int gmg_coarse_solve(gmg_problem* p, const void* b, void* x) {
+  if (!p || !b || !x || b == x) return GMG_ERR_INVALID_ARG;
+  return coarse_solve(p, b, x);
+}
+
+int gmg_vcycle(gmg_problem* p, void* x, const void* b) {
+  if (!p || !x || !b || x == b) return GMG_ERR_INVALID_ARG;
+  return vcycle_level(p, (int)p->levels.size() - 1, x, b);
+}
+
+int cg_gmg_solve(gmg_problem* p, double* u, const double* b, double rtol, int max_it,
+                 gmg_solve_stats* st) {
+  if (!p || !u || !b || u == b || !(rtol > 0.0) || max_it < 0) return GMG_ERR_INVALID_ARG;
+  const int Lf = (int)p->levels.size() - 1;
+  Level& F = p->levels[Lf];
+  const long long n = F.n_elems;
+  cudaStream_t s = p->stream;
+  double* sc = p->scal;
+  gmg_solve_stats local;
+  std::memset(&local, 0, sizeof(local));
+  double h_sc[S_COUNT];
+  auto fetch = [&]() -> int {
+    if (cudaMemcpyAsync(h_sc, sc, sizeof(h_sc), cudaMemcpyDeviceToHost, s) != cudaSuccess) return GMG_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return GMG_ERR_CUDA;
+    return GMG_OK;
+  };
+  auto precondition = [&]() -> int {  // z = V(r)
+    if (p->esize == 8) return vcycle_level(p, Lf, p->cg_z, p->cg_r);
+    CHECK(launch_convert_f64_f32(n, p->cg_r, (float*)F.b, s));
+    CHECK(vcycle_level(p, Lf, F.u, F.b));
+    return launch_convert_f32_f64(n, (const float*)F.u, p->cg_z, s);
+  };
+  auto finish = [&](int status) -> int {
+    if (st) *st = local;
+    return status;
+  };
+  // r = b - A u
+  ApplyLaunch al;
+  al.g = F.g;
+  al.alpha = -op_scale(F);
+  al.beta = 1.0;
+  CHECK(launch_apply<double>(al, u, p->cg_r, b, s));
+  CHECK(launch_dot(n, b, b, p->partial, sc + S_BB, s));
+  CHECK(launch_dot(n, p->cg_r, p->cg_r, p->partial, sc + S_RR, s));
+  CHECK(fetch());
+  const double bnorm = std::sqrt(h_sc[S_BB]);
+  double rnorm = std::sqrt(h_sc[S_RR]);
+  if (!std::isfinite(bnorm) || !std::isfinite(rnorm)) return finish(GMG_ERR_NONFINITE);
+  local.initial_residual = rnorm;
+  local.final_residual = rnorm;
+  local.relative_residual = bnorm > 0 ? rnorm / bnorm : 0.0;
+  local.residual_history[0] = local.relative_residual;
+  if (rnorm <= rtol * bnorm || bnorm == 0.0) {
+    local.converged = 1;
+    return finish(GMG_OK);
+  }
+  CHECK(precondition());
+  if (cudaMemcpyAsync(p->cg_p, p->cg_z, n * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return finish(GMG_ERR_CUDA);
+  CHECK(launch_dot(n, p->cg_r, p->cg_z, p->partial, sc + S_RZ, s));
+  al.alpha = op_scale(F);
+  al.beta = 0.0;
+  for (int it = 1; it <= max_it; ++it) {
+    CHECK(launch_apply<double>(al, p->cg_p, p->cg_q, nullptr, s));
+    CHECK(launch_dot(n, p->cg_p, p->cg_q, p->partial, sc + S_PQ, s));
+    CHECK(launch_cg_update(n, u, p->cg_r, p->cg_p, p->cg_q, sc + S_RZ, sc + S_PQ, p->partial,
+                           sc + S_RR, s));
+    CHECK(fetch());
+    if (!std::isfinite(h_sc[S_RZ]) || !std::isfinite(h_sc[S_PQ]) || !std::isfinite(h_sc[S_RR]))
+      return finish(GMG_ERR_NONFINITE);
+    if (!(h_sc[S_RZ] > 0.0) || !(h_sc[S_PQ] > 0.0)) return finish(GMG_ERR_BREAKDOWN);
+    rnorm = std::sqrt(h_sc[S_RR]);
+    local.iterations = it;
+    local.final_residual = rnorm;
+    local.relative_residual = rnorm / bnorm;
+    if (it < 64) local.residual_history[it] = local.relative_residual;
+    if (rnorm <= rtol * bnorm) {
+      local.converged = 1;
+      return finish(GMG_OK);
+    }
+    CHECK(precondition());
+    CHECK(launch_dot(n, p->cg_r, p->cg_z, p->partial, sc + S_RZN, s));
+    CHECK(launch_cg_direction(n, p->cg_p, p->cg_z, sc + S_RZN, sc + S_RZ, s));
+    if (cudaMemcpyAsync(sc + S_RZ, sc + S_RZN, 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return finish(GMG_ERR_CUDA);
+  }
+  return finish(GMG_ERR_NOT_CONVERGED);
+}
+
+}  // extern "C"

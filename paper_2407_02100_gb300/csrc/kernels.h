@@ -1,0 +1,87 @@
+// Host-visible launchers of the CUDA kernels (internal to the library; the
+// public C ABI is include/gmg.h).  Every launcher enqueues on `stream` and
+// returns a gmg_status code.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace gmg {
+
+// Geometry of one level vector: N nodes per direction, pitches in elements.
+struct LevelGeom {
+  int dim, k, n;      // dimension, degree, cells per direction
+  int N;              // nodes per direction = n k + 1
+  int py;             // element stride of the y index
+  long long pz;       // element stride of the z index (3D)
+};
+
+// One colour of the patch sweep.  Patches of colour c sit at vertices
+// v_a = first[a] + 2 i_a, i_a < count[a] (first[a] = 1 if bit a of c is
+// set, else 2).
+struct PatchLaunch {
+  LevelGeom g;
+  int first[3];
+  int count[3];
+  int n_patches;
+  double sb;          // h^{2-d}: scales b to the unit-cell operator
+  double omega;       // damping of the scatter
+};
+
+// y = alpha * (A_ref x) + beta * bvec on owned interior nodes, where A_ref is
+// the level operator assembled from unit cells (A = h^{d-2} A_ref).
+struct ApplyLaunch {
+  LevelGeom g;
+  double alpha, beta;
+};
+
+// One 1D contraction along `axis` of a (up to) 3-index array:
+//   out[o + out_off] (+)= sum_w coef[(o_ax % R) * W + w] * in[i]
+// where along the contracted axis the input index is
+//   ((o_ax + shift) / R) * S + off + w   (skipped if outside [0, in_dim[axis]))
+// with coefficient row (o_ax + shift) % R, and along the other axes it is
+// o + in_off.  Output counts per axis are cnt[]; strides are in elements.
+struct AxisOp {
+  int axis;
+  int cnt[3];
+  int in_dim[3];
+  long long in_stride[3];
+  int in_off[3];
+  long long out_stride[3];
+  int out_off[3];
+  int R, S, off, W;
+  int shift;
+  int accumulate;
+};
+
+template <typename T>
+int upload_patch_tables(int k, const double* Mp, const double* Kp, const double* That,
+                        const double* Mc, const double* Kc, cudaStream_t s);
+template <typename T>
+int launch_patch_colour(const PatchLaunch& pl, T* u, const T* b, const T* dinv, cudaStream_t s);
+template <typename T>
+int launch_apply(const ApplyLaunch& al, const T* x, T* y, const T* bvec, cudaStream_t s);
+
+template <typename T>
+int launch_axis_op(const AxisOp& op, const T* in, T* out, const T* coef, cudaStream_t s);
+template <typename T>
+int launch_scale(long long n, T* x, const T* d, cudaStream_t s);  // x *= d
+// element-type conversions over n elements
+int launch_convert_f64_f32(long long n, const double* x, float* y, cudaStream_t s);
+int launch_convert_f32_f64(long long n, const float* x, double* y, cudaStream_t s);
+
+// FP64 reductions: partial sums per block into `partial` (>= kReduceBlocks
+// doubles) then a single-block sum into `result` (device scalar).
+constexpr int kReduceBlocks = 1024;
+int launch_dot(long long n, const double* x, const double* y, double* partial, double* result,
+               cudaStream_t s);
+// x += alpha p, r -= alpha q with alpha = num/den read from device scalars;
+// also the partial sums of r.r into `partial` and their total into `result`.
+int launch_cg_update(long long n, double* x, double* r, const double* p, const double* q,
+                     const double* num, const double* den, double* partial, double* result,
+                     cudaStream_t s);
+// p = z + (num/den) p
+int launch_cg_direction(long long n, double* p, const double* z, const double* num,
+                        const double* den, cudaStream_t s);
+
+}  // namespace gmg

@@ -1,0 +1,112 @@
+// Launchers for one scalar type; included after patch_kernels.cuh by
+// patch_f64.cu / patch_f32.cu.
+#pragma once
+#include <algorithm>
+#include <vector>
+
+#include "../../include/gmg.h"
+
+namespace gmg {
+namespace GMG_NS {
+
+constexpr int kSweepThreads = 128;
+constexpr int kApplyThreads = 128;
+
+// cells per tile edge of the operator kernel
+constexpr int apply_bc(int dim, int k) {
+  return dim == 3 ? (k == 1 ? 8 : k == 2 ? 4 : k <= 4 ? 2 : 1)
+                  : (k == 1 ? 16 : k == 2 ? 8 : k <= 4 ? 4 : 2);
+}
+
+template <typename KernelT>
+static int prepare(KernelT kern, int smem) {
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+      return GMG_ERR_CUDA;
+  }
+  return GMG_OK;
+}
+
+template <int DIM, int K>
+static int patch_impl(const PatchLaunch& pl, T* u, const T* b, const T* dinv, cudaStream_t s) {
+  using D = PatchDims<DIM, K>;
+  auto kern = patch_colour_kernel<DIM, K, kSweepThreads>;
+  if (prepare(kern, D::SMEM_BYTES) != GMG_OK) return GMG_ERR_CUDA;
+  if (pl.n_patches <= 0) return GMG_OK;
+  int grid = std::min(pl.n_patches, 1 << 30);
+  kern<<<grid, kSweepThreads, D::SMEM_BYTES, s>>>(u, b, dinv, pl);
+  return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+}
+
+template <int DIM, int K>
+static int apply_impl(const ApplyLaunch& al, const T* x, T* y, const T* bvec, cudaStream_t s) {
+  constexpr int BC = apply_bc(DIM, K);
+  using D = ApplyDims<DIM, K, BC>;
+  auto kern = apply_kernel<DIM, K, BC, kApplyThreads>;
+  if (prepare(kern, D::SMEM_BYTES) != GMG_OK) return GMG_ERR_CUDA;
+  long long tiles = (al.g.n + BC - 1) / BC;
+  long long ntile = DIM == 3 ? tiles * tiles * tiles : tiles * tiles;
+  int grid = (int)std::min<long long>(ntile, 1 << 30);
+  kern<<<grid, kApplyThreads, D::SMEM_BYTES, s>>>(x, y, bvec, al);
+  return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+}
+
+#define GMG_DISPATCH(FN, DIMV, KV, ...)                                  \
+  switch ((DIMV) * 16 + (KV)) {                                          \
+    case 2 * 16 + 1: return FN<2, 1>(__VA_ARGS__);                       \
+    case 2 * 16 + 2: return FN<2, 2>(__VA_ARGS__);                       \
+    case 2 * 16 + 3: return FN<2, 3>(__VA_ARGS__);                       \
+    case 2 * 16 + 4: return FN<2, 4>(__VA_ARGS__);                       \
+    case 2 * 16 + 5: return FN<2, 5>(__VA_ARGS__);                       \
+    case 2 * 16 + 6: return FN<2, 6>(__VA_ARGS__);                       \
+    case 2 * 16 + 7: return FN<2, 7>(__VA_ARGS__);                       \
+    case 2 * 16 + 8: return FN<2, 8>(__VA_ARGS__);                       \
+    case 3 * 16 + 1: return FN<3, 1>(__VA_ARGS__);                       \
+    case 3 * 16 + 2: return FN<3, 2>(__VA_ARGS__);                       \
+    case 3 * 16 + 3: return FN<3, 3>(__VA_ARGS__);                       \
+    case 3 * 16 + 4: return FN<3, 4>(__VA_ARGS__);                       \
+    case 3 * 16 + 5: return FN<3, 5>(__VA_ARGS__);                       \
+    case 3 * 16 + 6: return FN<3, 6>(__VA_ARGS__);                       \
+    case 3 * 16 + 7: return FN<3, 7>(__VA_ARGS__);                       \
+    case 3 * 16 + 8: return FN<3, 8>(__VA_ARGS__);                       \
+    default: return GMG_ERR_INVALID_ARG;                                 \
+  }
+
+static int upload(int k, const double* Mp, const double* Kp, const double* That, const double* Mc,
+                  const double* Kc) {
+  if (k < 1 || k > 8) return GMG_ERR_INVALID_ARG;
+  const int C = 2 * k + 1, M = 2 * k - 1;
+  std::vector<T> mp(M * C), kp(M * C), tt(M * M), mc((k + 1) * (k + 1)), kc((k + 1) * (k + 1));
+  for (int i = 0; i < M * C; ++i) { mp[i] = (T)Mp[i]; kp[i] = (T)Kp[i]; }
+  for (int i = 0; i < M * M; ++i) tt[i] = (T)That[i];
+  for (int i = 0; i < (k + 1) * (k + 1); ++i) { mc[i] = (T)Mc[i]; kc[i] = (T)Kc[i]; }
+  cudaError_t e = cudaSuccess;
+  e = e == cudaSuccess ? cudaMemcpyToSymbol(c_Mp, mp.data(), mp.size() * sizeof(T), off_patch(k) * sizeof(T)) : e;
+  e = e == cudaSuccess ? cudaMemcpyToSymbol(c_Kp, kp.data(), kp.size() * sizeof(T), off_patch(k) * sizeof(T)) : e;
+  e = e == cudaSuccess ? cudaMemcpyToSymbol(c_T, tt.data(), tt.size() * sizeof(T), off_t(k) * sizeof(T)) : e;
+  e = e == cudaSuccess ? cudaMemcpyToSymbol(c_Mc, mc.data(), mc.size() * sizeof(T), off_cell(k) * sizeof(T)) : e;
+  e = e == cudaSuccess ? cudaMemcpyToSymbol(c_Kc, kc.data(), kc.size() * sizeof(T), off_cell(k) * sizeof(T)) : e;
+  return e == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+}
+
+}  // namespace GMG_NS
+
+template <>
+int upload_patch_tables<GMG_T>(int k, const double* Mp, const double* Kp, const double* That,
+                               const double* Mc, const double* Kc, cudaStream_t) {
+  return GMG_NS::upload(k, Mp, Kp, That, Mc, Kc);
+}
+
+template <>
+int launch_patch_colour<GMG_T>(const PatchLaunch& pl, GMG_T* u, const GMG_T* b, const GMG_T* dinv,
+                               cudaStream_t s) {
+  GMG_DISPATCH(GMG_NS::patch_impl, pl.g.dim, pl.g.k, pl, u, b, dinv, s)
+}
+
+template <>
+int launch_apply<GMG_T>(const ApplyLaunch& al, const GMG_T* x, GMG_T* y, const GMG_T* bvec,
+                        cudaStream_t s) {
+  GMG_DISPATCH(GMG_NS::apply_impl, al.g.dim, al.g.k, al, x, y, bvec, s)
+}
+
+}  // namespace gmg

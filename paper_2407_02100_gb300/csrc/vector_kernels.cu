@@ -1,0 +1,187 @@
+// Grid transfer (tensor-product 1D contractions along one axis), diagonal
+// scaling, precision conversion and the FP64 vector kernels of the outer CG.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "../../include/gmg.h"
+#include "kernels.h"
+
+namespace gmg {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  return (int)std::max<long long>(1, std::min<long long>(b, 152LL * 16));
+}
+
+// out[o + out_off] (+)= sum_w coef[(o_ax % R) W + w] in[(o_ax / R) S + off + w]
+// with one thread per output element (x index fastest, so that loads and
+// stores along the contiguous axis coalesce).
+template <typename T>
+__global__ void axis_op_kernel(const T* __restrict__ in, T* __restrict__ out,
+                               const T* __restrict__ coef, AxisOp op) {
+  const long long total = (long long)op.cnt[0] * op.cnt[1] * op.cnt[2];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int o[3];
+    o[0] = (int)(e % op.cnt[0]);
+    long long r = e / op.cnt[0];
+    o[1] = (int)(r % op.cnt[1]);
+    o[2] = (int)(r / op.cnt[1]);
+    long long ibase = 0, obase = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      obase += (long long)(o[a] + op.out_off[a]) * op.out_stride[a];
+      if (a != op.axis) ibase += (long long)(o[a] + op.in_off[a]) * op.in_stride[a];
+    }
+    const int oa = o[op.axis] + op.shift;
+    const int start = (oa / op.R) * op.S + op.off;
+    const T* c = coef + (oa % op.R) * op.W;
+    const long long sa = op.in_stride[op.axis];
+    const int lim = op.in_dim[op.axis];
+    T acc = T(0);
+    for (int w = 0; w < op.W; ++w) {
+      int i = start + w;
+      if (i >= 0 && i < lim) acc += c[w] * in[ibase + i * sa];
+    }
+    if (op.accumulate) out[obase] += acc;
+    else out[obase] = acc;
+  }
+}
+
+template <typename T>
+__global__ void scale_kernel(long long n, T* __restrict__ x, const T* __restrict__ d) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] *= d[i];
+}
+
+__global__ void f64_to_f32_kernel(long long n, const double* __restrict__ x, float* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
+__global__ void f32_to_f64_kernel(long long n, const float* __restrict__ x, double* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+
+// block-level sum (kThreads threads) of one value per thread
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double warp_part[kThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) warp_part[wid] = v;
+  __syncthreads();
+  v = (threadIdx.x < kThreads / 32) ? warp_part[threadIdx.x] : 0.0;
+  if (wid == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  return v;  // valid in thread 0
+}
+
+__global__ void dot_partial_kernel(long long n, const double* __restrict__ x,
+                                   const double* __restrict__ y, double* __restrict__ partial) {
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    s += x[i] * y[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// single block: result = sum of `count` partials (fixed order: deterministic)
+__global__ void final_sum_kernel(int count, const double* __restrict__ partial, double* __restrict__ result) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) s += partial[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) *result = s;
+}
+
+__global__ void cg_update_kernel(long long n, double* __restrict__ x, double* __restrict__ r,
+                                 const double* __restrict__ p, const double* __restrict__ q,
+                                 const double* __restrict__ num, const double* __restrict__ den,
+                                 double* __restrict__ partial) {
+  const double alpha = *num / *den;
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    s += ri * ri;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void cg_direction_kernel(long long n, double* __restrict__ p, const double* __restrict__ z,
+                                    const double* __restrict__ num, const double* __restrict__ den) {
+  const double beta = *num / *den;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+inline int status() { return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA; }
+
+}  // namespace
+
+template <typename T>
+int launch_axis_op(const AxisOp& op, const T* in, T* out, const T* coef, cudaStream_t s) {
+  long long total = (long long)op.cnt[0] * op.cnt[1] * op.cnt[2];
+  if (total <= 0) return GMG_OK;
+  axis_op_kernel<T><<<grid_for(total, kThreads), kThreads, 0, s>>>(in, out, coef, op);
+  return status();
+}
+template int launch_axis_op<double>(const AxisOp&, const double*, double*, const double*, cudaStream_t);
+template int launch_axis_op<float>(const AxisOp&, const float*, float*, const float*, cudaStream_t);
+
+template <typename T>
+int launch_scale(long long n, T* x, const T* d, cudaStream_t s) {
+  if (n <= 0) return GMG_OK;
+  scale_kernel<T><<<grid_for(n, kThreads), kThreads, 0, s>>>(n, x, d);
+  return status();
+}
+template int launch_scale<double>(long long, double*, const double*, cudaStream_t);
+template int launch_scale<float>(long long, float*, const float*, cudaStream_t);
+
+int launch_convert_f64_f32(long long n, const double* x, float* y, cudaStream_t s) {
+  f64_to_f32_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, x, y);
+  return status();
+}
+int launch_convert_f32_f64(long long n, const float* x, double* y, cudaStream_t s) {
+  f32_to_f64_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, x, y);
+  return status();
+}
+
+int launch_dot(long long n, const double* x, const double* y, double* partial, double* result,
+               cudaStream_t s) {
+  int g = std::min(grid_for(n, kThreads), kReduceBlocks);
+  dot_partial_kernel<<<g, kThreads, 0, s>>>(n, x, y, partial);
+  final_sum_kernel<<<1, kThreads, 0, s>>>(g, partial, result);
+  return status();
+}
+
+int launch_cg_update(long long n, double* x, double* r, const double* p, const double* q,
+                     const double* num, const double* den, double* partial, double* result,
+                     cudaStream_t s) {
+  int g = std::min(grid_for(n, kThreads), kReduceBlocks);
+  cg_update_kernel<<<g, kThreads, 0, s>>>(n, x, r, p, q, num, den, partial);
+  final_sum_kernel<<<1, kThreads, 0, s>>>(g, partial, result);
+  return status();
+}
+
+int launch_cg_direction(long long n, double* p, const double* z, const double* num,
+                        const double* den, cudaStream_t s) {
+  cg_direction_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, p, z, num, den);
+  return status();
+}
+
+}  // namespace gmg

@@ -1,0 +1,242 @@
+"""Thin ctypes binding of libgmg.so (C ABI declared in include/gmg.h).
+
+Argument marshalling only: every step of the smoother, the transfer, the
+V-cycle and the CG runs in the library's CUDA kernels.  PyTorch provides
+device memory (tensors) and the stream.  The binding never falls back to a
+CPU path: if the library is missing or cannot be loaded, every call raises.
+
+The functions carry the C names (gmg_create, gmg_smooth, ...); ``Problem``
+is a small convenience wrapper around them.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgmg.so")
+
+GMG_OK = 0
+GMG_FP64 = 0
+GMG_FP32 = 1
+STATUS = {0: "ok", -1: "invalid argument", -2: "device out of memory", -3: "CUDA error",
+          -4: "non-finite value in solver", -5: "CG breakdown", -6: "not converged",
+          -7: "unsupported"}
+
+EXPORTS = ["gmg_create", "gmg_destroy", "gmg_vector_layout", "gmg_level_info",
+           "gmg_apply_operator", "gmg_apply_operator_f64", "gmg_smooth", "gmg_smooth_colour",
+           "gmg_restrict", "gmg_prolongate_add", "gmg_coarse_solve", "gmg_vcycle",
+           "cg_gmg_solve", "gmg_patch_fd_1d", "gmg_status_string"]
+
+
+class GmgDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("degree", ctypes.c_int), ("n_cells", ctypes.c_int),
+                ("n_levels", ctypes.c_int), ("precision", ctypes.c_int), ("damping", ctypes.c_double),
+                ("pre_sweeps", ctypes.c_int), ("post_sweeps", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class GmgSolveStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("initial_residual", ctypes.c_double), ("final_residual", ctypes.c_double),
+                ("relative_residual", ctypes.c_double), ("residual_history", ctypes.c_double * 64)]
+
+
+class GmgError(RuntimeError):
+    def __init__(self, fn, status):
+        super().__init__(f"{fn} failed: {STATUS.get(status, status)} ({status})")
+        self.status = status
+
+
+_LIB = None
+
+
+def lib():
+    """Load libgmg.so (built in-tree by paper_2407_02100_gb300.build)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2407_02100_gb300.build` (no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+        sig = {
+            "gmg_create": [ctypes.POINTER(GmgDesc), ctypes.POINTER(vp)],
+            "gmg_destroy": [vp],
+            "gmg_vector_layout": [vp, i, ctypes.POINTER(ll), ctypes.POINTER(i), ctypes.POINTER(i),
+                                  ctypes.POINTER(ll)],
+            "gmg_level_info": [vp, i, ctypes.POINTER(i), ctypes.POINTER(i)],
+            "gmg_apply_operator": [vp, i, vp, vp],
+            "gmg_apply_operator_f64": [vp, i, vp, vp],
+            "gmg_smooth": [vp, i, vp, vp, i, i],
+            "gmg_smooth_colour": [vp, i, vp, vp, i],
+            "gmg_restrict": [vp, i, vp, vp],
+            "gmg_prolongate_add": [vp, i, vp, vp],
+            "gmg_coarse_solve": [vp, vp, vp],
+            "gmg_vcycle": [vp, vp, vp],
+            "cg_gmg_solve": [vp, vp, vp, d, i, ctypes.POINTER(GmgSolveStats)],
+            "gmg_patch_fd_1d": [i, vp, vp, vp, vp],
+            "gmg_status_string": [i],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_char_p if name == "gmg_status_string" else ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def _check(fn, st):
+    if st != GMG_OK:
+        raise GmgError(fn, st)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------------------
+# C names
+
+def gmg_create(dim, degree, n_cells, n_levels=0, precision=GMG_FP64, damping=1.0,
+               pre_sweeps=1, post_sweeps=1, stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    desc = GmgDesc(dim, degree, n_cells, n_levels, precision, damping, pre_sweeps, post_sweeps,
+                   ctypes.c_void_p(stream))
+    h = ctypes.c_void_p()
+    _check("gmg_create", lib().gmg_create(ctypes.byref(desc), ctypes.byref(h)))
+    return h
+
+
+def gmg_destroy(h):
+    _check("gmg_destroy", lib().gmg_destroy(h))
+
+
+def gmg_vector_layout(h, level):
+    n, N, py, pz = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+    _check("gmg_vector_layout", lib().gmg_vector_layout(h, level, ctypes.byref(n), ctypes.byref(N),
+                                                          ctypes.byref(py), ctypes.byref(pz)))
+    return n.value, N.value, py.value, pz.value
+
+
+def gmg_level_info(h, level):
+    n, L = ctypes.c_int(), ctypes.c_int()
+    _check("gmg_level_info", lib().gmg_level_info(h, level, ctypes.byref(n), ctypes.byref(L)))
+    return n.value, L.value
+
+
+def gmg_apply_operator(h, level, x, y):
+    _check("gmg_apply_operator", lib().gmg_apply_operator(h, level, _ptr(x), _ptr(y)))
+
+
+def gmg_apply_operator_f64(h, level, x, y):
+    _check("gmg_apply_operator_f64", lib().gmg_apply_operator_f64(h, level, _ptr(x), _ptr(y)))
+
+
+def gmg_smooth(h, level, u, b, n_sweeps=1, reverse=False):
+    _check("gmg_smooth", lib().gmg_smooth(h, level, _ptr(u), _ptr(b), n_sweeps, int(bool(reverse))))
+
+
+def gmg_smooth_colour(h, level, u, b, colour):
+    _check("gmg_smooth_colour", lib().gmg_smooth_colour(h, level, _ptr(u), _ptr(b), colour))
+
+
+def gmg_restrict(h, fine_level, fine, coarse):
+    _check("gmg_restrict", lib().gmg_restrict(h, fine_level, _ptr(fine), _ptr(coarse)))
+
+
+def gmg_prolongate_add(h, coarse_level, coarse, fine):
+    _check("gmg_prolongate_add", lib().gmg_prolongate_add(h, coarse_level, _ptr(coarse), _ptr(fine)))
+
+
+def gmg_coarse_solve(h, b, x):
+    _check("gmg_coarse_solve", lib().gmg_coarse_solve(h, _ptr(b), _ptr(x)))
+
+
+def gmg_vcycle(h, x, b):
+    _check("gmg_vcycle", lib().gmg_vcycle(h, _ptr(x), _ptr(b)))
+
+
+def cg_gmg_solve(h, u, b, rtol=1e-10, max_it=100, raise_on_error=True):
+    st = GmgSolveStats()
+    status = lib().cg_gmg_solve(h, _ptr(u), _ptr(b), rtol, max_it, ctypes.byref(st))
+    if raise_on_error:
+        _check("cg_gmg_solve", status)
+    return status, st
+
+
+def gmg_patch_fd_1d(degree):
+    """Host-only: (M, K, T, lambda) of the two-unit-cell patch (numpy)."""
+    m = 2 * degree - 1
+    M, K, T = (np.zeros((m, m)) for _ in range(3))
+    lam = np.zeros(m)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check("gmg_patch_fd_1d", lib().gmg_patch_fd_1d(degree, p(M), p(K), p(T), p(lam)))
+    return M, K, T, lam
+
+
+def gmg_status_string(status):
+    return lib().gmg_status_string(status).decode()
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+
+class Problem:
+    """Owns one gmg_problem.  Vectors are torch CUDA tensors in the padded
+    layout of include/gmg.h; to_device/from_device convert from/to the dense
+    (n k + 1)^dim node arrays (x index fastest) used by the tests."""
+
+    def __init__(self, dim, degree, n_cells, n_levels=0, precision=GMG_FP64, damping=1.0,
+                 pre_sweeps=1, post_sweeps=1, stream=None):
+        import torch
+        self.torch = torch
+        self.dim, self.degree, self.n_cells = dim, degree, n_cells
+        self.precision = precision
+        self.dtype = torch.float64 if precision == GMG_FP64 else torch.float32
+        self.h = gmg_create(dim, degree, n_cells, n_levels, precision, damping, pre_sweeps,
+                            post_sweeps, stream)
+        self.n_levels = gmg_level_info(self.h, 0)[1]
+
+    def close(self):
+        if self.h is not None:
+            gmg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def finest(self):
+        return self.n_levels - 1
+
+    def layout(self, level=None):
+        return gmg_vector_layout(self.h, self.finest if level is None else level)
+
+    def zeros(self, level=None, dtype=None):
+        n = self.layout(level)[0]
+        return self.torch.zeros(n, dtype=dtype or self.dtype, device="cuda")
+
+    def to_device(self, dense, level=None, dtype=None):
+        """Dense node array (N^dim, x fastest) -> padded device vector."""
+        n, N, py, pz = self.layout(level)
+        t = self.torch
+        dense = t.as_tensor(np.asarray(dense)).to(dtype or self.dtype)
+        out = t.zeros(n, dtype=dtype or self.dtype)
+        if self.dim == 2:
+            out.view(N, py)[:, :N] = dense.view(N, N)
+        else:
+            out.view(N, N, py)[:, :, :N] = dense.view(N, N, N)
+        return out.cuda()
+
+    def from_device(self, vec, level=None):
+        """Padded device vector -> dense float64 numpy node array."""
+        n, N, py, pz = self.layout(level)
+        v = vec.detach().to("cpu", self.torch.float64)
+        if self.dim == 2:
+            return v.view(N, py)[:, :N].reshape(-1).numpy().copy()
+        return v.view(N, N, py)[:, :, :N].reshape(-1).numpy().copy()

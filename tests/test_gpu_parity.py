@@ -1,0 +1,158 @@
+"""GPU parity: every step of the hot path through the C ABI against the FP64
+oracle on the same seeded inputs, element by element.
+
+Tolerance (FP64): relative 1e-12 in the 2-norm and 1e-11 of the largest
+entry elementwise.  The fast-diagonalisation local solve and the oracle's
+LU solve round differently; their gap grows with the condition number of
+A_j, which stays below ~1e4 for k <= 8, i.e. ~1e-12 relative.
+Sizes span several operator tiles and ragged tails (n not a multiple of the
+tile edge), Q1..Q8, 2D and 3D, boundary patches included."""
+import numpy as np
+import pytest
+
+from oracle.mesh import Mesh
+from oracle.multigrid import Multigrid, prolongation
+from oracle.smoother import PatchSmoother
+from paper_2407_02100_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def gmg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2407_02100_gb300 import build, gmg as g
+    build.build()
+    return g
+
+
+def close(got, ref, rtol=RTOL, what=""):
+    scale = np.abs(ref).max()
+    err2 = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300)
+    errm = np.abs(got - ref).max() / max(scale, 1e-300)
+    assert err2 <= rtol and errm <= 10 * rtol, f"{what}: rel2={err2:.3e} relmax={errm:.3e}"
+
+
+OPERATOR_CASES = [(2, 1, 37), (2, 2, 20), (2, 3, 9), (2, 5, 7), (2, 8, 5),
+                  (3, 1, 10), (3, 2, 10), (3, 3, 5), (3, 4, 5), (3, 5, 3), (3, 7, 3)]
+
+
+@pytest.mark.parametrize("dim,k,n", OPERATOR_CASES)
+def test_apply_operator(gmg, dim, k, n):
+    m = Mesh(dim, k, n)
+    P = gmg.Problem(dim, k, n, n_levels=1)
+    x = inputs.random_nodal(dim, k, n, 101)
+    y = P.zeros()
+    gmg.gmg_apply_operator(P.h, 0, P.to_device(x), y)
+    close(P.from_device(y), m.assemble() @ x, what="A x")
+
+
+SWEEP_CASES = [(2, 1, 9), (2, 2, 32), (2, 3, 11), (2, 4, 6), (2, 6, 5), (2, 8, 4),
+               (3, 1, 9), (3, 2, 7), (3, 3, 6), (3, 4, 5), (3, 5, 4), (3, 6, 3), (3, 8, 3)]
+
+
+@pytest.mark.parametrize("dim,k,n", SWEEP_CASES)
+def test_each_colour_step(gmg, dim, k, n):
+    m = Mesh(dim, k, n)
+    s = PatchSmoother(m)
+    P = gmg.Problem(dim, k, n, n_levels=1)
+    u0 = inputs.random_nodal(dim, k, n, 201)
+    b = inputs.random_nodal(dim, k, n, 202)
+    bd = P.to_device(b)
+    for c in range(m.n_colours):
+        ud = P.to_device(u0)
+        gmg.gmg_smooth_colour(P.h, 0, ud, bd, c)
+        ref = s.colour_step(u0.copy(), b, c)
+        close(P.from_device(ud), ref, what=f"colour {c}")
+
+
+@pytest.mark.parametrize("dim,k,n", SWEEP_CASES)
+@pytest.mark.parametrize("reverse", [False, True])
+def test_full_sweep(gmg, dim, k, n, reverse):
+    m = Mesh(dim, k, n)
+    s = PatchSmoother(m)
+    P = gmg.Problem(dim, k, n, n_levels=1)
+    u0 = inputs.random_nodal(dim, k, n, 301)
+    b = inputs.random_nodal(dim, k, n, 302)
+    ud = P.to_device(u0)
+    gmg.gmg_smooth(P.h, 0, ud, P.to_device(b), 2, reverse)
+    ref = s.sweep(s.sweep(u0, b, reverse), b, reverse)
+    close(P.from_device(ud), ref, what="two sweeps")
+
+
+@pytest.mark.parametrize("omega", [0.7, 1.3])
+def test_damped_sweep(gmg, omega):
+    dim, k, n = 3, 2, 6
+    m = Mesh(dim, k, n)
+    s = PatchSmoother(m, omega)
+    P = gmg.Problem(dim, k, n, n_levels=1, damping=omega)
+    u0 = inputs.random_nodal(dim, k, n, 401)
+    b = inputs.random_nodal(dim, k, n, 402)
+    ud = P.to_device(u0)
+    gmg.gmg_smooth(P.h, 0, ud, P.to_device(b), 1, False)
+    close(P.from_device(ud), s.sweep(u0, b), what="damped sweep")
+
+
+TRANSFER_CASES = [(2, 1, 8), (2, 2, 6), (2, 3, 4), (2, 5, 4), (3, 1, 6), (3, 2, 4), (3, 3, 4), (3, 4, 2)]
+
+
+@pytest.mark.parametrize("dim,k,n", TRANSFER_CASES)
+def test_restrict_and_prolongate(gmg, dim, k, n):
+    c, f = Mesh(dim, k, n // 2), Mesh(dim, k, n)
+    Pm = prolongation(c, f)
+    P = gmg.Problem(dim, k, n, n_levels=2)
+    rf = inputs.random_nodal(dim, k, n, 501)
+    ec = inputs.random_nodal(dim, k, n // 2, 502)
+    uf = inputs.random_nodal(dim, k, n, 503)
+    out_c = P.zeros(0)
+    gmg.gmg_restrict(P.h, 1, P.to_device(rf, 1), out_c)
+    close(P.from_device(out_c, 0), Pm.T @ rf, what="restrict")
+    ufd = P.to_device(uf, 1)
+    gmg.gmg_prolongate_add(P.h, 0, P.to_device(ec, 0), ufd)
+    close(P.from_device(ufd, 1), uf + Pm @ ec, what="prolongate")
+
+
+@pytest.mark.parametrize("dim,k,n", [(2, 2, 4), (2, 4, 3), (2, 8, 2), (3, 1, 4), (3, 2, 3), (3, 4, 2), (3, 7, 2)])
+def test_coarse_solve(gmg, dim, k, n):
+    m = Mesh(dim, k, n)
+    A = m.assemble()
+    P = gmg.Problem(dim, k, n, n_levels=1)
+    b = inputs.random_nodal(dim, k, n, 601)
+    x = P.zeros(0)
+    gmg.gmg_coarse_solve(P.h, P.to_device(b, 0), x)
+    xg = P.from_device(x, 0)
+    inner = m.interior_nodes()
+    ref = np.zeros_like(b)
+    ref[inner] = np.linalg.solve(A[inner][:, inner].toarray(), b[inner])
+    close(xg, ref, what="coarse solve")
+
+
+VCYCLE_CASES = [(2, 2, 32, 3), (2, 3, 16, 3), (2, 1, 16, 4), (3, 2, 8, 3), (3, 3, 4, 2), (3, 4, 4, 2)]
+
+
+@pytest.mark.parametrize("dim,k,n,L", VCYCLE_CASES)
+def test_vcycle(gmg, dim, k, n, L):
+    mg = Multigrid(dim, k, n, L)
+    P = gmg.Problem(dim, k, n, n_levels=L)
+    b = inputs.random_nodal(dim, k, n, 701)
+    x = P.zeros()
+    gmg.gmg_vcycle(P.h, x, P.to_device(b))
+    close(P.from_device(x), mg.vcycle(b), what="V-cycle")
+
+
+@pytest.mark.parametrize("dim,k,n,L", VCYCLE_CASES)
+def test_pcg(gmg, dim, k, n, L):
+    mg = Multigrid(dim, k, n, L)
+    P = gmg.Problem(dim, k, n, n_levels=L)
+    b = inputs.random_nodal(dim, k, n, 801)
+    u = P.zeros(dtype=__import__("torch").float64)
+    status, st = gmg.cg_gmg_solve(P.h, u, P.to_device(b, dtype=__import__("torch").float64), 1e-10, 100)
+    xo, its, hist = mg.pcg(b, rtol=1e-10)
+    assert st.converged == 1 and st.relative_residual <= 1e-10
+    assert abs(st.iterations - its) <= 1, (st.iterations, its)
+    got = P.from_device(u)
+    assert np.linalg.norm(got - xo) <= 1e-8 * np.linalg.norm(xo)
