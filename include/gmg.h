@@ -100,7 +100,8 @@ int gmg_level_info(const gmg_problem* p, int level, int* n_cells, int* n_levels)
  * eq. "matrix"; evaluated by sum factorisation of the tensor-product cell
  * operators, App. A.1).  x, y: device vectors of the problem's level-vector
  * type (double for GMG_FP64, float for GMG_FP32), distinct buffers.
- * Dirichlet rows of y are written as zero. */
+ * Only interior nodes of y are written; its Dirichlet and padding entries
+ * must already be zero (as for every vector argument). */
 int gmg_apply_operator(gmg_problem* p, int level, const void* x, void* y);
 
 /* Same operator in double precision regardless of the problem precision
@@ -158,6 +159,10 @@ int cg_gmg_solve(gmg_problem* p, double* u, const double* b, double rtol, int ma
  * row-major, caller-allocated, of (2k-1)^2 (M, K, T) and 2k-1 (lambda)
  * doubles; any may be NULL. */
 int gmg_patch_fd_1d(int degree, double* M, double* K, double* T, double* lambda);
+
+/* Number of CUDA kernels this library has enqueued since it was loaded
+ * (host-side counter, all problems and devices).  Host-only. */
+long long gmg_kernel_launch_count(void);
 
 /* Human-readable name of a status code (static storage). */
 const char* gmg_status_string(int status);

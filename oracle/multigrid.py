@@ -14,39 +14,45 @@ outer iteration (x_0 = 0, stop at ||r|| <= rtol ||b||).
 """
 import numpy as np
 import scipy.linalg as sla
+import scipy.sparse as sp
 
 from . import fe
 from .mesh import Mesh
 from .smoother import PatchSmoother
 
 
-def prolongation(coarse: Mesh, fine: Mesh):
-    """Dense embedding matrix P (fine nodes x coarse nodes), Dirichlet rows
-    and columns zeroed.  Small meshes only."""
+def prolongation(coarse: Mesh, fine: Mesh, sparse=False):
+    """Embedding matrix P (fine nodes x coarse nodes), Dirichlet rows and
+    columns zeroed; dense, or scipy CSR when sparse=True (same entries)."""
     assert fine.dim == coarse.dim and fine.k == coarse.k and fine.n == 2 * coarse.n
     k, dim = coarse.k, coarse.dim
     xi = fe.gauss_lobatto_points(k)
     X = fine.node_coordinates()                       # [n_fine, dim]
-    P = np.zeros((fine.n_nodes, coarse.n_nodes))
     loc = np.indices((k + 1,) * dim).reshape(dim, -1)[::-1].T
+    rows, cols, vals = [], [], []
     for f in range(fine.n_nodes):
         cell = np.minimum(np.floor(X[f] / coarse.h).astype(int), coarse.n - 1)
         t = X[f] / coarse.h - cell                    # reference coordinate in [0,1]
-        vals = np.ones(len(loc))
+        v = np.ones(len(loc))
         for a in range(dim):
-            vals *= fe.lagrange_values(xi, t[a])[0][loc[:, a]]
-        cols = coarse.flat(cell[None, :] * k + loc)
-        P[f, cols] = vals
-    fb, cb = fine.boundary_mask(), coarse.boundary_mask()
-    P[fb, :] = 0.0
-    P[:, cb] = 0.0
-    return P
+            v *= fe.lagrange_values(xi, t[a])[0][loc[:, a]]
+        rows.append(np.full(len(loc), f))
+        cols.append(coarse.flat(cell[None, :] * k + loc))
+        vals.append(v)
+    P = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(fine.n_nodes, coarse.n_nodes)).tocsr()
+    # every (fine, coarse) pair appears once: the fine node is assigned to one
+    # coarse cell, whose local nodes are distinct
+    keep_f = sp.diags((~fine.boundary_mask()).astype(np.float64))
+    keep_c = sp.diags((~coarse.boundary_mask()).astype(np.float64))
+    P = (keep_f @ P @ keep_c).tocsr()
+    return P if sparse else P.toarray()
 
 
 class Multigrid:
     """Level hierarchy with assembled operators (small meshes only)."""
 
-    def __init__(self, dim, degree, n_cells, n_levels, omega=1.0):
+    def __init__(self, dim, degree, n_cells, n_levels, omega=1.0, sparse=True):
         self.meshes = []
         for l in range(n_levels):
             n = n_cells // 2 ** (n_levels - 1 - l)
@@ -54,7 +60,7 @@ class Multigrid:
                 raise ValueError("n_cells not divisible for this many levels")
             self.meshes.append(Mesh(dim, degree, n))
         self.A = [m.assemble() for m in self.meshes]
-        self.P = [prolongation(self.meshes[l], self.meshes[l + 1]) for l in range(n_levels - 1)]
+        self.P = [prolongation(self.meshes[l], self.meshes[l + 1], sparse) for l in range(n_levels - 1)]
         self.smoothers = [PatchSmoother(m, omega) for m in self.meshes]
         inner0 = self.meshes[0].interior_nodes()
         self._inner0 = inner0

@@ -4,6 +4,7 @@
 // only builds tables on the host, owns device buffers and sequences launches.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -14,6 +15,10 @@
 #include "setup.h"
 
 using namespace gmg;
+
+static std::atomic<long long> g_launches{0};
+void gmg::count_launch(int n) { g_launches += n; }
+long long gmg::launch_count() { return g_launches.load(); }
 
 namespace {
 
@@ -310,6 +315,8 @@ int vcycle_level(gmg_problem* p, int l, void* x, const void* b) {
 }  // namespace
 
 extern "C" {
+
+long long gmg_kernel_launch_count(void) { return launch_count(); }
 
 const char* gmg_status_string(int s) {
   switch (s) {

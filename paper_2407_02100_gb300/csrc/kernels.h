@@ -54,6 +54,11 @@ struct AxisOp {
   int accumulate;
 };
 
+// Host-side count of kernel launches made by this library (all launchers
+// call count_launch once per kernel they enqueue).
+void count_launch(int n = 1);
+long long launch_count();
+
 template <typename T>
 int upload_patch_tables(int k, const double* Mp, const double* Kp, const double* That,
                         const double* Mc, const double* Kc, cudaStream_t s);

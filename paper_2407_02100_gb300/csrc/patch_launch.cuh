@@ -35,6 +35,7 @@ static int patch_impl(const PatchLaunch& pl, T* u, const T* b, const T* dinv, cu
   if (pl.n_patches <= 0) return GMG_OK;
   int grid = std::min(pl.n_patches, 1 << 30);
   kern<<<grid, kSweepThreads, D::SMEM_BYTES, s>>>(u, b, dinv, pl);
+  count_launch();
   return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
 }
 
@@ -48,6 +49,7 @@ static int apply_impl(const ApplyLaunch& al, const T* x, T* y, const T* bvec, cu
   long long ntile = DIM == 3 ? tiles * tiles * tiles : tiles * tiles;
   int grid = (int)std::min<long long>(ntile, 1 << 30);
   kern<<<grid, kApplyThreads, D::SMEM_BYTES, s>>>(x, y, bvec, al);
+  count_launch();
   return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
 }
 

@@ -129,7 +129,10 @@ __global__ void cg_direction_kernel(long long n, double* __restrict__ p, const d
     p[i] = z[i] + beta * p[i];
 }
 
-inline int status() { return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA; }
+inline int status(int launches = 1) {
+  count_launch(launches);
+  return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+}
 
 }  // namespace
 
@@ -166,7 +169,7 @@ int launch_dot(long long n, const double* x, const double* y, double* partial, d
   int g = std::min(grid_for(n, kThreads), kReduceBlocks);
   dot_partial_kernel<<<g, kThreads, 0, s>>>(n, x, y, partial);
   final_sum_kernel<<<1, kThreads, 0, s>>>(g, partial, result);
-  return status();
+  return status(2);
 }
 
 int launch_cg_update(long long n, double* x, double* r, const double* p, const double* q,
@@ -175,7 +178,7 @@ int launch_cg_update(long long n, double* x, double* r, const double* p, const d
   int g = std::min(grid_for(n, kThreads), kReduceBlocks);
   cg_update_kernel<<<g, kThreads, 0, s>>>(n, x, r, p, q, num, den, partial);
   final_sum_kernel<<<1, kThreads, 0, s>>>(g, partial, result);
-  return status();
+  return status(2);
 }
 
 int launch_cg_direction(long long n, double* p, const double* z, const double* num,

@@ -26,7 +26,7 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "device out of memory", -3: "CUDA
 EXPORTS = ["gmg_create", "gmg_destroy", "gmg_vector_layout", "gmg_level_info",
            "gmg_apply_operator", "gmg_apply_operator_f64", "gmg_smooth", "gmg_smooth_colour",
            "gmg_restrict", "gmg_prolongate_add", "gmg_coarse_solve", "gmg_vcycle",
-           "cg_gmg_solve", "gmg_patch_fd_1d", "gmg_status_string"]
+           "cg_gmg_solve", "gmg_patch_fd_1d", "gmg_kernel_launch_count", "gmg_status_string"]
 
 
 class GmgDesc(ctypes.Structure):
@@ -75,12 +75,14 @@ def lib():
             "gmg_vcycle": [vp, vp, vp],
             "cg_gmg_solve": [vp, vp, vp, d, i, ctypes.POINTER(GmgSolveStats)],
             "gmg_patch_fd_1d": [i, vp, vp, vp, vp],
+            "gmg_kernel_launch_count": [],
             "gmg_status_string": [i],
         }
         for name, args in sig.items():
             f = getattr(L, name)
             f.argtypes = args
-            f.restype = ctypes.c_char_p if name == "gmg_status_string" else ctypes.c_int
+            f.restype = {"gmg_status_string": ctypes.c_char_p,
+                         "gmg_kernel_launch_count": ctypes.c_longlong}.get(name, ctypes.c_int)
         _LIB = L
     return _LIB
 
@@ -174,6 +176,10 @@ def gmg_patch_fd_1d(degree):
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     _check("gmg_patch_fd_1d", lib().gmg_patch_fd_1d(degree, p(M), p(K), p(T), p(lam)))
     return M, K, T, lam
+
+
+def gmg_kernel_launch_count():
+    return lib().gmg_kernel_launch_count()
 
 
 def gmg_status_string(status):

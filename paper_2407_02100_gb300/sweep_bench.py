@@ -1,0 +1,58 @@
+"""Smoother and operator micro-benchmark (CUDA events on the problem's stream).
+
+Times finest-level multiplicative patch sweeps (all colours, gmg_smooth) and
+matrix-free operator applications on one uniform level, for a chosen
+dimension, degree, mesh and precision, and prints the rates:
+
+    python -m paper_2407_02100_gb300.sweep_bench --dim 3 --degree 4 --n 64 --precision fp64
+
+It is also the driver used for ncu captures of the patch kernel (a few
+launches on a workload whose vectors exceed L2).
+"""
+import argparse
+import json
+
+import torch
+
+from . import build, gmg, inputs
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--dim", type=int, default=3)
+    ap.add_argument("--degree", type=int, default=4)
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--sweeps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=2)
+    a = ap.parse_args()
+    build.build()
+    prec = gmg.GMG_FP64 if a.precision == "fp64" else gmg.GMG_FP32
+    P = gmg.Problem(a.dim, a.degree, a.n, n_levels=1, precision=prec)
+    u = P.to_device(inputs.random_nodal(a.dim, a.degree, a.n, 1))
+    b = P.to_device(inputs.random_nodal(a.dim, a.degree, a.n, 2))
+    y = P.zeros()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        for _ in range(a.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps * 1e-3
+
+    t_sweep = timed(lambda: gmg.gmg_smooth(P.h, 0, u, b, 1, False), a.sweeps)
+    t_apply = timed(lambda: gmg.gmg_apply_operator(P.h, 0, u, y), a.sweeps)
+    nodes = (a.n * a.degree + 1) ** a.dim
+    print(json.dumps({"dim": a.dim, "degree": a.degree, "n_cells": a.n, "precision": a.precision,
+                      "nodes": nodes, "sweep_ms": t_sweep * 1e3, "sweep_mdofs": nodes / t_sweep / 1e6,
+                      "apply_ms": t_apply * 1e3, "apply_mdofs": nodes / t_apply / 1e6}))
+    P.close()
+
+
+if __name__ == "__main__":
+    main()
