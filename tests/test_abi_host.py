@@ -26,7 +26,8 @@ def gmg():
 def _declared_functions():
     src = open(os.path.join(ROOT, "include", "gmg.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\*?\s+\*?(\w+)\s*\(", src, flags=re.M)))
+    pat = r"^\s*(?:const\s+)?(?:long\s+long|\w+)\*?\s+\*?(\w+)\s*\("
+    return sorted(set(re.findall(pat, src, flags=re.M)))
 
 
 def test_library_exports_every_declared_function(gmg):
