@@ -152,6 +152,25 @@ int gmg_vcycle(gmg_problem* p, void* x, const void* b);
 int cg_gmg_solve(gmg_problem* p, double* u, const double* b, double rtol, int max_it,
                  gmg_solve_stats* stats);
 
+/* gmg_smooth without a problem object and without allocating device memory
+ * (the paper has no counterpart: this is a deployment variant).  For callers
+ * that cannot call cudaMalloc -- their device memory belongs to another
+ * allocator (a framework arena or pool), or they must not incur cudaMalloc's
+ * implicit device-wide synchronisation.  Runs n_sweeps FP64 smoothing steps
+ * on one uniform level of n_cells cells per direction (same layout, colour
+ * order and damping semantics as gmg_smooth), in place on the caller's
+ * double device vectors u and b, on `stream` (a cudaStream_t).
+ * The fast-diagonalisation diagonal lives in a library-owned static device
+ * array of (2*8-1)^3 doubles (27 KB, kept on every GPU that loads the
+ * library until exit); patches needing more are rejected with
+ * GMG_ERR_INVALID_ARG, as are bad dim/degree/n_cells/damping/pointers.
+ * The first call on a device looks the array's address up (once, with that
+ * device current); make that first call before any stream capture.  Every
+ * call rewrites the part of the array it uses; calls that overlap on the GPU
+ * (different streams, no ordering between them) race on it. */
+int gmg_smooth_noalloc(int dim, int degree, int n_cells, double damping, double* u,
+                       const double* b, int n_sweeps, int reverse, void* stream);
+
 /* Host-only set-up math exposed for testing: the 1D fast-diagonalisation
  * data of one vertex patch built from two cells of unit width (App. A.3):
  * M, K = interior (2k-1)x(2k-1) mass and stiffness of the two-cell 1D

@@ -26,7 +26,8 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "device out of memory", -3: "CUDA
 EXPORTS = ["gmg_create", "gmg_destroy", "gmg_vector_layout", "gmg_level_info",
            "gmg_apply_operator", "gmg_apply_operator_f64", "gmg_smooth", "gmg_smooth_colour",
            "gmg_restrict", "gmg_prolongate_add", "gmg_coarse_solve", "gmg_vcycle",
-           "cg_gmg_solve", "gmg_patch_fd_1d", "gmg_kernel_launch_count", "gmg_status_string"]
+           "cg_gmg_solve", "gmg_patch_fd_1d", "gmg_kernel_launch_count", "gmg_status_string",
+           "gmg_smooth_noalloc"]
 
 
 class GmgDesc(ctypes.Structure):
@@ -76,6 +77,7 @@ def lib():
             "cg_gmg_solve": [vp, vp, vp, d, i, ctypes.POINTER(GmgSolveStats)],
             "gmg_patch_fd_1d": [i, vp, vp, vp, vp],
             "gmg_kernel_launch_count": [],
+            "gmg_smooth_noalloc": [i, i, i, d, vp, vp, i, i, vp],
             "gmg_status_string": [i],
         }
         for name, args in sig.items():
@@ -176,6 +178,19 @@ def gmg_patch_fd_1d(degree):
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     _check("gmg_patch_fd_1d", lib().gmg_patch_fd_1d(degree, p(M), p(K), p(T), p(lam)))
     return M, K, T, lam
+
+
+def gmg_smooth_noalloc(dim, degree, n_cells, u, b, n_sweeps=1, reverse=False, damping=1.0,
+                       stream=None):
+    """FP64 smoothing of one level without a problem object and without
+    device allocation (for callers whose device memory belongs to another
+    allocator); u, b: float64 CUDA tensors in the level layout."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check("gmg_smooth_noalloc", lib().gmg_smooth_noalloc(dim, degree, n_cells, damping, _ptr(u), _ptr(b),
+                                                          n_sweeps, int(bool(reverse)),
+                                                          ctypes.c_void_p(stream)))
 
 
 def gmg_kernel_launch_count():
