@@ -337,7 +337,7 @@ int gmg_patch_fd_1d(int k, double* M, double* K, double* T, double* lambda) {
   const int m = 2 * k - 1;
   std::vector<double> Mi, Ki, Ti, li;
   assembled_1d(k, 2, 1, m, 1, m, Mi, Ki);
-  if (!generalized_eigen(m, Mi, Ki, Ti, li)) return GMG_ERR_INVALID_ARG;
+  if (!generalized_eigen_mirror(m, Mi, Ki, Ti, li)) return GMG_ERR_INVALID_ARG;
   if (M) std::memcpy(M, Mi.data(), sizeof(double) * m * m);
   if (K) std::memcpy(K, Ki.data(), sizeof(double) * m * m);
   if (T) std::memcpy(T, Ti.data(), sizeof(double) * m * m);
@@ -389,7 +389,7 @@ static int create_impl(const gmg_desc* d, gmg_problem* p) {
   cell_matrices_1d(k, Mc, Kc);
   assembled_1d(k, 2, 1, m, 0, C, Mp, Kp);
   assembled_1d(k, 2, 1, m, 1, m, Mi, Ki);
-  if (!generalized_eigen(m, Mi, Ki, Tp, lp)) return GMG_ERR_INVALID_ARG;
+  if (!generalized_eigen_mirror(m, Mi, Ki, Tp, lp)) return GMG_ERR_INVALID_ARG;
   CHECK(upload_patch_tables<double>(k, Mp.data(), Kp.data(), Tp.data(), Mc.data(), Kc.data(), p->stream));
   CHECK(upload_patch_tables<float>(k, Mp.data(), Kp.data(), Tp.data(), Mc.data(), Kc.data(), p->stream));
   const int nint = dim == 3 ? m * m * m : m * m;

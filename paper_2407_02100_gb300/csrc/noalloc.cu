@@ -76,7 +76,7 @@ extern "C" int gmg_smooth_noalloc(int dim, int degree, int n_cells, double dampi
   cell_matrices_1d(k, Mc, Kc);
   assembled_1d(k, 2, 1, m, 0, C, Mp, Kp);
   assembled_1d(k, 2, 1, m, 1, m, Mi, Ki);
-  if (!generalized_eigen(m, Mi, Ki, Tp, lp)) return GMG_ERR_INVALID_ARG;
+  if (!generalized_eigen_mirror(m, Mi, Ki, Tp, lp)) return GMG_ERR_INVALID_ARG;
   st = upload_patch_tables<double>(k, Mp.data(), Kp.data(), Tp.data(), Mc.data(), Kc.data(), s);
   if (st != GMG_OK) return st;
   std::vector<double> dinv(nint);

@@ -65,92 +65,152 @@ struct PatchDims {
   static constexpr int SMEM_BYTES = (SA + SB) * (int)sizeof(T);
 };
 
-// y[i] = sum_j E[i][j] x[j] over the band, E = patch table at compile-time
-// offset; i = 0..M-1 (closure row i+1)
-template <int K>
-__device__ __forceinline__ T patch_row(const T* E, int i, const T (&x)[2 * K + 1]) {
+// acc + sign * sum_j E[i][j] x[j] over the band of closure row i+1 of a
+// two-cell patch table E (compile-time offset); i = 0..M-1
+template <int K, bool NEG = false>
+__device__ __forceinline__ T patch_row(const T* E, int i, const T (&x)[2 * K + 1], T acc = T(0)) {
   constexpr int C = 2 * K + 1;
-  T acc = T(0);
 #pragma unroll
   for (int j = 0; j < C; ++j) {
-    if (j >= band_lo(i + 1, K) && j <= band_hi(i + 1, K)) acc = fma(E[i * C + j], x[j], acc);
+    if (j >= band_lo(i + 1, K) && j <= band_hi(i + 1, K))
+      acc = fma(NEG ? -E[i * C + j] : E[i * C + j], x[j], acc);
   }
   return acc;
 }
 
-// FD transform along one axis, in place on a line of M values at stride s:
-// forward (TRANSPOSE = true): y_i = sum_j T[j][i] x_j; backward: y_i = sum_j T[i][j] x_j
+// FD transform along one axis, in place on a line of M = 2K-1 values at
+// stride s, using the mirror symmetry of the eigenvectors: modes 0..K-1 are
+// even (T[M-1-j][i] = T[j][i]), modes K..M-1 odd (T[M-1-j][i] = -T[j][i]).
+// forward (TRANSPOSE = true): y_i = sum_j T[j][i] x_j
+// backward:                   x_j = sum_i T[j][i] y_i
 template <int K, bool TRANSPOSE>
 __device__ __forceinline__ void fd_line(T* base, int s) {
-  constexpr int M = 2 * K - 1;
+  constexpr int M = 2 * K - 1, c = K - 1;
   const T* Tm = c_T + off_t(K);
-  T x[M];
+  if (TRANSPOSE) {
+    T sv[K], dv[K > 1 ? K - 1 : 1];
 #pragma unroll
-  for (int j = 0; j < M; ++j) x[j] = base[j * s];
+    for (int j = 0; j < c; ++j) {
+      T a = base[j * s], b = base[(M - 1 - j) * s];
+      sv[j] = a + b;
+      dv[j] = a - b;
+    }
+    sv[c] = base[c * s];
 #pragma unroll
-  for (int i = 0; i < M; ++i) {
-    T acc = T(0);
+    for (int i = 0; i < K; ++i) {  // even modes
+      T acc = T(0);
 #pragma unroll
-    for (int j = 0; j < M; ++j) acc = fma(TRANSPOSE ? Tm[j * M + i] : Tm[i * M + j], x[j], acc);
-    base[i * s] = acc;
+      for (int j = 0; j <= c; ++j) acc = fma(Tm[j * M + i], sv[j], acc);
+      base[i * s] = acc;
+    }
+#pragma unroll
+    for (int i = K; i < M; ++i) {  // odd modes
+      T acc = T(0);
+#pragma unroll
+      for (int j = 0; j < c; ++j) acc = fma(Tm[j * M + i], dv[j], acc);
+      base[i * s] = acc;
+    }
+  } else {
+    T y[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) y[i] = base[i * s];
+#pragma unroll
+    for (int j = 0; j < c; ++j) {
+      T e = T(0), o = T(0);
+#pragma unroll
+      for (int i = 0; i < K; ++i) e = fma(Tm[j * M + i], y[i], e);
+#pragma unroll
+      for (int i = K; i < M; ++i) o = fma(Tm[j * M + i], y[i], o);
+      base[j * s] = e + o;
+      base[(M - 1 - j) * s] = e - o;
+    }
+    T e = T(0);
+#pragma unroll
+    for (int i = 0; i < K; ++i) e = fma(Tm[c * M + i], y[i], e);
+    base[c * s] = e;
   }
 }
 
-// Apply the FD transform along every axis of an M^DIM block in shared memory.
-template <int DIM, int K, bool TRANSPOSE, int NT>
-__device__ __forceinline__ void fd_all_axes(T* R) {
+// Apply the FD transform along every axis of the M^DIM blocks of PPC patches
+// (block q at R + q * stride).
+template <int DIM, int K, bool TRANSPOSE, int NT, int PPC>
+__device__ __forceinline__ void fd_all_axes(T* R, int stride, const bool* valid) {
   constexpr int M = 2 * K - 1;
-  if (DIM == 2) {
-    for (int l = threadIdx.x; l < M; l += NT) fd_line<K, TRANSPOSE>(R + l * M, 1);      // x
-    __syncthreads();
-    for (int l = threadIdx.x; l < M; l += NT) fd_line<K, TRANSPOSE>(R + l, M);          // y
-    __syncthreads();
-  } else {
-    for (int l = threadIdx.x; l < M * M; l += NT) fd_line<K, TRANSPOSE>(R + l * M, 1);  // x
-    __syncthreads();
-    for (int l = threadIdx.x; l < M * M; l += NT) {
-      int x = l % M, z = l / M;
-      fd_line<K, TRANSPOSE>(R + x + z * M * M, M);                                       // y
+  constexpr int L = DIM == 3 ? M * M : M;
+#pragma unroll
+  for (int axis = 0; axis < DIM; ++axis) {
+    for (int idx = threadIdx.x; idx < PPC * L; idx += NT) {
+      const int q = idx / L, l = idx % L;
+      if (!valid[q]) continue;
+      T* Rq = R + q * stride;
+      if (DIM == 2) {
+        if (axis == 0) fd_line<K, TRANSPOSE>(Rq + l * M, 1);
+        else fd_line<K, TRANSPOSE>(Rq + l, M);
+      } else {
+        if (axis == 0) fd_line<K, TRANSPOSE>(Rq + l * M, 1);
+        else if (axis == 1) fd_line<K, TRANSPOSE>(Rq + (l % M) + (l / M) * M * M, M);
+        else fd_line<K, TRANSPOSE>(Rq + l, M * M);
+      }
     }
     __syncthreads();
-    for (int l = threadIdx.x; l < M * M; l += NT) fd_line<K, TRANSPOSE>(R + l, M * M);  // z
-    __syncthreads();
   }
 }
 
-template <int DIM, int K, int NT>
+// One colour of the sweep: each CTA takes PPC consecutive patches of the
+// colour; every stage distributes the lines of all its patches over the
+// threads, so partial warps are rare.
+template <int DIM, int K, int NT, int PPC>
 __global__ void __launch_bounds__(NT) patch_colour_kernel(T* __restrict__ u, const T* __restrict__ b,
                                                           const T* __restrict__ dinv, PatchLaunch pl) {
   using D = PatchDims<DIM, K>;
   constexpr int C = D::C, M = D::M;
+  constexpr int STRIDE = D::SA + D::SB;  // elements of shared memory per patch
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* A = reinterpret_cast<T*>(smem_raw);
-  T* B = A + D::SA;
+  T* const S = reinterpret_cast<T*>(smem_raw);
+  __shared__ long long s_origin[PPC];
+  __shared__ bool s_valid[PPC];
   const T* Mp = c_Mp + off_patch(K);
   const T* Kp = c_Kp + off_patch(K);
   const long long py = pl.g.py, pz = pl.g.pz;
   const T sb = (T)pl.sb;
+  const T om = (T)pl.omega;
+  const int ngroups = (pl.n_patches + PPC - 1) / PPC;
 
-  for (int pid = blockIdx.x; pid < pl.n_patches; pid += gridDim.x) {
-    int i0 = pid % pl.count[0];
-    int rest = pid / pl.count[0];
-    int i1 = rest % pl.count[1];
-    int i2 = DIM == 3 ? rest / pl.count[1] : 0;
-    const long long o0 = (long long)(pl.first[0] + 2 * i0 - 1) * K;
-    const long long o1 = (long long)(pl.first[1] + 2 * i1 - 1) * K;
-    const long long o2 = DIM == 3 ? (long long)(pl.first[2] + 2 * i2 - 1) * K : 0;
-    const long long origin = o0 + py * o1 + pz * o2;
+  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    if (threadIdx.x < PPC) {
+      const int pid = grp * PPC + threadIdx.x;
+      const bool ok = pid < pl.n_patches;
+      int i0 = 0, i1 = 0, i2 = 0;
+      if (ok) {
+        i0 = pid % pl.count[0];
+        const int rest = pid / pl.count[0];
+        i1 = rest % pl.count[1];
+        i2 = DIM == 3 ? rest / pl.count[1] : 0;
+      }
+      const long long o0 = (long long)(pl.first[0] + 2 * i0 - 1) * K;
+      const long long o1 = (long long)(pl.first[1] + 2 * i1 - 1) * K;
+      const long long o2 = DIM == 3 ? (long long)(pl.first[2] + 2 * i2 - 1) * K : 0;
+      s_origin[threadIdx.x] = o0 + py * o1 + pz * o2;
+      s_valid[threadIdx.x] = ok;
+    }
+    __syncthreads();
 
-    // ---- gather the closure (eq. "gather") ----
-    for (int t = threadIdx.x; t < D::NCLO; t += NT) {
-      int x = t % C, y = (t / C) % C, z = DIM == 3 ? t / (C * C) : 0;
-      A[t] = u[origin + x + py * y + pz * z];
+    // ---- gather the closures (eq. "gather") ----
+    for (int idx = threadIdx.x; idx < PPC * D::NCLO; idx += NT) {
+      const int q = idx / D::NCLO, t = idx % D::NCLO;
+      if (!s_valid[q]) continue;
+      const int x = t % C, y = (t / C) % C, z = DIM == 3 ? t / (C * C) : 0;
+      S[q * STRIDE + t] = u[s_origin[q] + x + py * y + pz * z];
     }
     __syncthreads();
 
     if (DIM == 3) {
-      // ---- stage z: P = Mp_z u, Q = Kp_z u   (dims x:C, y:C, z:M) ----
-      for (int l = threadIdx.x; l < C * C; l += NT) {
+      // ---- stage z: P = Mp_z u, Q = Kp_z u   (dims x:C, y:C, z:M, in B) ----
+      for (int idx = threadIdx.x; idx < PPC * C * C; idx += NT) {
+        const int q = idx / (C * C), l = idx % (C * C);
+        if (!s_valid[q]) continue;
+        const T* A = S + q * STRIDE;
+        T* B = S + q * STRIDE + D::SA;
         T x[C];
 #pragma unroll
         for (int j = 0; j < C; ++j) x[j] = A[l + j * C * C];
@@ -161,52 +221,55 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(T* __restrict__ u, con
         }
       }
       __syncthreads();
-      // ---- stage y: A1 = Mp_y P, A2 = Kp_y P + Mp_y Q   (dims x:C, y:M, z:M) ----
-      for (int l = threadIdx.x; l < C * M; l += NT) {
-        int x0 = l % C, z = l / C;
-        T p[C], q[C];
+      // ---- stage y: A1 = Mp_y P, A2 = Kp_y P + Mp_y Q   (dims x:C, y:M, z:M, in A) ----
+      for (int idx = threadIdx.x; idx < PPC * C * M; idx += NT) {
+        const int q = idx / (C * M), l = idx % (C * M);
+        if (!s_valid[q]) continue;
+        T* A = S + q * STRIDE;
+        const T* B = S + q * STRIDE + D::SA;
+        const int x0 = l % C, z = l / C;
+        T p[C], r[C];
 #pragma unroll
         for (int j = 0; j < C; ++j) {
           p[j] = B[x0 + j * C + z * C * C];
-          q[j] = B[C * C * M + x0 + j * C + z * C * C];
+          r[j] = B[C * C * M + x0 + j * C + z * C * C];
         }
 #pragma unroll
         for (int i = 0; i < M; ++i) {
           A[x0 + i * C + z * C * M] = patch_row<K>(Mp, i, p);
-          A[C * M * M + x0 + i * C + z * C * M] = patch_row<K>(Kp, i, p) + patch_row<K>(Mp, i, q);
+          A[C * M * M + x0 + i * C + z * C * M] = patch_row<K>(Mp, i, r, patch_row<K>(Kp, i, p));
         }
       }
       __syncthreads();
       // ---- stage x: r = sb b - (Kp_x A1 + Mp_x A2)   (dims M^3, into B) ----
-      for (int l = threadIdx.x; l < M * M; l += NT) {
-        int y = l % M, z = l / M;
+      for (int idx = threadIdx.x; idx < PPC * M * M; idx += NT) {
+        const int q = idx / (M * M), l = idx % (M * M);
+        if (!s_valid[q]) continue;
+        const T* A = S + q * STRIDE;
+        T* B = S + q * STRIDE + D::SA;
+        const int y = l % M, z = l / M;
         T a1[C], a2[C];
 #pragma unroll
         for (int j = 0; j < C; ++j) {
           a1[j] = A[j + C * (y + M * z)];
           a2[j] = A[C * M * M + j + C * (y + M * z)];
         }
-        const long long row = origin + 1 + py * (y + 1) + pz * (z + 1);
+        const long long row = s_origin[q] + 1 + py * (y + 1) + pz * (z + 1);
 #pragma unroll
-        for (int i = 0; i < M; ++i)
-          B[i + M * l] = sb * b[row + i] - (patch_row<K>(Kp, i, a1) + patch_row<K>(Mp, i, a2));
+        for (int i = 0; i < M; ++i) {
+          T acc = sb * b[row + i];
+          acc = patch_row<K, true>(Kp, i, a1, acc);
+          B[i + M * l] = patch_row<K, true>(Mp, i, a2, acc);
+        }
       }
       __syncthreads();
-      // ---- local solve by fast diagonalisation (in place on B) ----
-      fd_all_axes<3, K, true, NT>(B);
-      for (int t = threadIdx.x; t < D::NINT; t += NT) B[t] *= dinv[t];
-      __syncthreads();
-      fd_all_axes<3, K, false, NT>(B);
-      // ---- scatter (eq. "scatter") ----
-      const T om = (T)pl.omega;
-      for (int t = threadIdx.x; t < D::NINT; t += NT) {
-        int x = t % M, y = (t / M) % M, z = t / (M * M);
-        long long g = origin + (x + 1) + py * (y + 1) + pz * (z + 1);
-        u[g] = u[g] + om * B[t];
-      }
     } else {
       // ---- stage y: P = Mp_y u, Q = Kp_y u   (dims x:C, y:M, into B) ----
-      for (int l = threadIdx.x; l < C; l += NT) {
+      for (int idx = threadIdx.x; idx < PPC * C; idx += NT) {
+        const int q = idx / C, l = idx % C;
+        if (!s_valid[q]) continue;
+        const T* A = S + q * STRIDE;
+        T* B = S + q * STRIDE + D::SA;
         T x[C];
 #pragma unroll
         for (int j = 0; j < C; ++j) x[j] = A[l + j * C];
@@ -217,32 +280,50 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(T* __restrict__ u, con
         }
       }
       __syncthreads();
-      // ---- stage x: r = sb b - (Kp_x P + Mp_x Q)   (dims M^2, into A) ----
-      for (int l = threadIdx.x; l < M; l += NT) {
-        T p[C], q[C];
+      // ---- stage x: r = sb b - (Kp_x P + Mp_x Q)   (dims M^2, into A: the
+      // closure is consumed) ----
+      for (int idx = threadIdx.x; idx < PPC * M; idx += NT) {
+        const int q = idx / M, l = idx % M;
+        if (!s_valid[q]) continue;
+        T* A = S + q * STRIDE;
+        const T* B = S + q * STRIDE + D::SA;
+        T p[C], r[C];
 #pragma unroll
         for (int j = 0; j < C; ++j) {
           p[j] = B[j + C * l];
-          q[j] = B[C * M + j + C * l];
+          r[j] = B[C * M + j + C * l];
         }
-        const long long row = origin + 1 + py * (l + 1);
+        const long long row = s_origin[q] + 1 + py * (l + 1);
 #pragma unroll
-        for (int i = 0; i < M; ++i)
-          A[i + M * l] = sb * b[row + i] - (patch_row<K>(Kp, i, p) + patch_row<K>(Mp, i, q));
+        for (int i = 0; i < M; ++i) {
+          T acc = sb * b[row + i];
+          acc = patch_row<K, true>(Kp, i, p, acc);
+          A[i + M * l] = patch_row<K, true>(Mp, i, r, acc);
+        }
       }
       __syncthreads();
-      fd_all_axes<2, K, true, NT>(A);
-      for (int t = threadIdx.x; t < D::NINT; t += NT) A[t] *= dinv[t];
-      __syncthreads();
-      fd_all_axes<2, K, false, NT>(A);
-      const T om = (T)pl.omega;
-      for (int t = threadIdx.x; t < D::NINT; t += NT) {
-        int x = t % M, y = t / M;
-        long long g = origin + (x + 1) + py * (y + 1);
-        u[g] = u[g] + om * A[t];
-      }
     }
-    __syncthreads();  // shared buffers are reused by the next patch
+
+    // ---- local solve by fast diagonalisation, in place ----
+    T* R0 = DIM == 3 ? S + D::SA : S;  // r of patch 0 (3D: buffer B, 2D: buffer A)
+    fd_all_axes<DIM, K, true, NT, PPC>(R0, STRIDE, s_valid);
+    for (int idx = threadIdx.x; idx < PPC * D::NINT; idx += NT) {
+      const int q = idx / D::NINT, t = idx % D::NINT;
+      if (s_valid[q]) R0[q * STRIDE + t] *= dinv[t];
+    }
+    __syncthreads();
+    fd_all_axes<DIM, K, false, NT, PPC>(R0, STRIDE, s_valid);
+
+    // ---- scatter (eq. "scatter"): u_interior += omega d ----
+    for (int idx = threadIdx.x; idx < PPC * D::NINT; idx += NT) {
+      const int q = idx / D::NINT, t = idx % D::NINT;
+      if (!s_valid[q]) continue;
+      const int x = t % M, y = (t / M) % M;
+      long long g = s_origin[q] + (x + 1) + py * (y + 1);
+      if (DIM == 3) g += pz * (t / (M * M) + 1);
+      u[g] = fma(om, R0[q * STRIDE + t], u[g]);
+    }
+    __syncthreads();  // shared buffers and s_origin are reused by the next group
   }
 }
 

@@ -9,8 +9,14 @@
 namespace gmg {
 namespace GMG_NS {
 
-constexpr int kSweepThreads = 128;
 constexpr int kApplyThreads = 128;
+
+// patches per CTA and threads per CTA of the sweep kernel: enough lines per
+// stage to fill whole warps, shared memory per CTA kept near 32-64 KB
+constexpr int sweep_ppc(int dim, int k) {
+  return dim == 2 ? 8 : (k <= 2 ? 8 : k <= 4 ? 4 : k <= 6 ? 2 : 1);
+}
+constexpr int sweep_threads(int dim, int k) { return dim == 3 && k >= 6 ? 256 : 128; }
 
 // cells per tile edge of the operator kernel
 constexpr int apply_bc(int dim, int k) {
@@ -30,11 +36,13 @@ static int prepare(KernelT kern, int smem) {
 template <int DIM, int K>
 static int patch_impl(const PatchLaunch& pl, T* u, const T* b, const T* dinv, cudaStream_t s) {
   using D = PatchDims<DIM, K>;
-  auto kern = patch_colour_kernel<DIM, K, kSweepThreads>;
-  if (prepare(kern, D::SMEM_BYTES) != GMG_OK) return GMG_ERR_CUDA;
+  constexpr int PPC = sweep_ppc(DIM, K), NT = sweep_threads(DIM, K);
+  constexpr int SMEM = PPC * D::SMEM_BYTES;
+  auto kern = patch_colour_kernel<DIM, K, NT, PPC>;
+  if (prepare(kern, SMEM) != GMG_OK) return GMG_ERR_CUDA;
   if (pl.n_patches <= 0) return GMG_OK;
-  int grid = std::min(pl.n_patches, 1 << 30);
-  kern<<<grid, kSweepThreads, D::SMEM_BYTES, s>>>(u, b, dinv, pl);
+  int grid = std::min((pl.n_patches + PPC - 1) / PPC, 1 << 30);
+  kern<<<grid, NT, SMEM, s>>>(u, b, dinv, pl);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
 }

@@ -210,6 +210,55 @@ bool generalized_eigen(int n, const std::vector<double>& M, const std::vector<do
   return true;
 }
 
+bool generalized_eigen_mirror(int n, const std::vector<double>& M, const std::vector<double>& K,
+                              std::vector<double>& T, std::vector<double>& lambda) {
+  if (n % 2 == 0) return false;
+  const int c = (n - 1) / 2, ne = c + 1, no = c;
+  const double r = 1.0 / std::sqrt(2.0);
+  // orthonormal mirror bases: E (n x ne), O (n x no)
+  std::vector<double> E(n * ne, 0.0), O(n * no, 0.0);
+  for (int j = 0; j < c; ++j) {
+    E[j * ne + j] = r;
+    E[(n - 1 - j) * ne + j] = r;
+    O[j * no + j] = r;
+    O[(n - 1 - j) * no + j] = -r;
+  }
+  E[c * ne + c] = 1.0;
+  auto project = [&](const std::vector<double>& B, const std::vector<double>& A, int nb) {
+    std::vector<double> out(nb * nb, 0.0);  // B^T A B
+    for (int i = 0; i < nb; ++i)
+      for (int j = 0; j < nb; ++j) {
+        double s2 = 0.0;
+        for (int p = 0; p < n; ++p)
+          for (int q = 0; q < n; ++q) s2 += B[p * nb + i] * A[p * n + q] * B[q * nb + j];
+        out[i * nb + j] = s2;
+      }
+    return out;
+  };
+  std::vector<double> Te, le, To, lo;
+  if (!generalized_eigen(ne, project(E, M, ne), project(E, K, ne), Te, le)) return false;
+  if (no > 0 && !generalized_eigen(no, project(O, M, no), project(O, K, no), To, lo)) return false;
+  T.assign(n * n, 0.0);
+  lambda.assign(n, 0.0);
+  for (int i = 0; i < ne; ++i) {
+    lambda[i] = le[i];
+    for (int j = 0; j < n; ++j) {
+      double s2 = 0.0;
+      for (int p = 0; p < ne; ++p) s2 += E[j * ne + p] * Te[p * ne + i];
+      T[j * n + i] = s2;
+    }
+  }
+  for (int i = 0; i < no; ++i) {
+    lambda[ne + i] = lo[i];
+    for (int j = 0; j < n; ++j) {
+      double s2 = 0.0;
+      for (int p = 0; p < no; ++p) s2 += O[j * no + p] * To[p * no + i];
+      T[j * n + ne + i] = s2;
+    }
+  }
+  return true;
+}
+
 void prolongation_cell_1d(int k, std::vector<double>& P) {
   std::vector<double> xi = gauss_lobatto(k);
   P.assign((2 * k + 1) * (k + 1), 0.0);

@@ -34,6 +34,15 @@ void assembled_1d(int k, int ncells, int r0, int nr, int c0, int nc,
 bool generalized_eigen(int n, const std::vector<double>& M, const std::vector<double>& K,
                        std::vector<double>& T, std::vector<double>& lambda);
 
+// Same eigenproblem for matrices that commute with the reflection
+// i -> n-1-i (n odd), solved separately on the even and the odd subspace so
+// that the eigenvectors are exactly mirror-symmetric: columns 0..(n-1)/2 of
+// T are even (T[n-1-j][i] = T[j][i]), the remaining (n-1)/2 columns are odd
+// (T[n-1-j][i] = -T[j][i], zero at the centre row).  Lambda follows the same
+// order.
+bool generalized_eigen_mirror(int n, const std::vector<double>& M, const std::vector<double>& K,
+                              std::vector<double>& T, std::vector<double>& lambda);
+
 // Embedding prolongation of one coarse unit cell split in two fine cells:
 // P[r][p] = phi^coarse_p(x_r) for the 2k+1 fine nodes r of the coarse cell
 // ((2k+1) x (k+1), row-major).
