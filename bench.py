@@ -280,6 +280,39 @@ def run_ours(args):
     gmg.gmg_apply_operator_f64(P.h, P.finest, u, r)
     rel_res = float(torch.linalg.vector_norm(b - r) / torch.linalg.vector_norm(b))
 
+    # ---- mixed precision: FP32 smoother / V-cycle inside the FP64 CG, same
+    # workload, same accuracy target ----
+    P32 = gmg.Problem(DIM, DEGREE, N_CELLS, n_levels=0, precision=gmg.GMG_FP32)
+    u32 = P32.zeros(dtype=torch.float64)
+    st32 = None
+    for _ in range(args.warmup):
+        u32.zero_()
+        _, st32 = gmg.cg_gmg_solve(P32.h, u32, b, RTOL, 100)
+    torch.cuda.synchronize()
+    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    m0.record(stream)
+    for _ in range(args.steps):
+        u32.zero_()
+        _, st32 = gmg.cg_gmg_solve(P32.h, u32, b, RTOL, 100)
+    m1.record(stream)
+    torch.cuda.synchronize()
+    ms32 = m0.elapsed_time(m1) / args.steps
+    diff32 = float(torch.linalg.vector_norm(u32 - u) / torch.linalg.vector_norm(u))
+    gmg.gmg_apply_operator_f64(P32.h, P32.finest, u32, r)
+    res32 = float(torch.linalg.vector_norm(b - r) / torch.linalg.vector_norm(b))
+    us32 = P32.zeros()
+    bs32 = b.to(torch.float32)
+    for _ in range(2):
+        gmg.gmg_smooth(P32.h, P32.finest, us32, bs32, 1, False)
+    torch.cuda.synchronize()
+    s0.record(stream)
+    for _ in range(n_sweeps):
+        gmg.gmg_smooth(P32.h, P32.finest, us32, bs32, 1, False)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    sweep32_s = s0.elapsed_time(s1) * 1e-3 / n_sweeps
+    P32.close()
+
     if rank != 0:
         P.close()
         if dist is not None:
@@ -316,6 +349,13 @@ def run_ours(args):
         "smoother": {"ms_per_sweep": sweep_s * 1e3, "mdofs": nodes / sweep_s / 1e6,
                      "hbm_gbs_algorithmic": hbm_gbs, "patches": patches,
                      "flop_per_patch": FLOP_PER_PATCH},
+        "fp32_mixed": {"time_to_solution_ms": ms32, "mdofs": nodes / (ms32 * 1e-3) / 1e6,
+                       "cg_iterations": st32.iterations, "final_rel_residual": res32,
+                       "rel_diff_vs_fp64_solution": diff32,
+                       "speedup_vs_fp64": ms_per_step / ms32,
+                       "smoother_ms_per_sweep": sweep32_s * 1e3,
+                       "smoother_mdofs": nodes / sweep32_s / 1e6,
+                       "smoother_hbm_gbs_algorithmic": 12 * nodes / sweep32_s / 1e9},
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
                      "traffic": None, "kernel": "patch_colour_kernel<3,4> (FP64)",
