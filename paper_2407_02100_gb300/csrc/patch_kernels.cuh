@@ -52,181 +52,225 @@ __constant__ T c_Kc[kCellTotal];
 __host__ __device__ constexpr int band_lo(int c, int K) { return c > K ? K : 0; }
 __host__ __device__ constexpr int band_hi(int c, int K) { return c < K ? K : 2 * K; }
 
-template <int DIM, int K>
-struct PatchDims {
-  static constexpr int C = 2 * K + 1;
-  static constexpr int M = 2 * K - 1;
-  static constexpr int NCLO = DIM == 3 ? C * C * C : C * C;
-  static constexpr int NINT = DIM == 3 ? M * M * M : M * M;
-  // buffer A: closure, then (3D) the stage-y results, (2D) r and the FD work
-  static constexpr int SA = DIM == 3 ? cmax(C * C * C, 2 * C * M * M) : C * C;
-  // buffer B: stage-z (3D) / stage-y (2D) results, then (3D) r and FD work
-  static constexpr int SB = DIM == 3 ? cmax(2 * C * C * M, M * M * M) : 2 * C * M;
-  static constexpr int SMEM_BYTES = (SA + SB) * (int)sizeof(T);
-};
 
-// acc + sign * sum_j E[i][j] x[j] over the band of closure row i+1 of a
-// two-cell patch table E (compile-time offset); i = 0..M-1
-template <int K, bool NEG = false>
-__device__ __forceinline__ T patch_row(const T* E, int i, const T (&x)[2 * K + 1], T acc = T(0)) {
+// acc + sign * sum_j E[i][j] x[j] over the band of closure row i+1 of the
+// two-cell patch matrix E = M_p (KIND 0) or K_p (KIND 1); i = 0..M-1.  The
+// __constant__ tables are indexed directly with compile-time offsets so that
+// every coefficient is an immediate constant-bank operand.
+template <int K, int KIND, bool NEG = false>
+__device__ __forceinline__ T patch_row(int i, const T (&x)[2 * K + 1], T acc = T(0)) {
   constexpr int C = 2 * K + 1;
 #pragma unroll
   for (int j = 0; j < C; ++j) {
-    if (j >= band_lo(i + 1, K) && j <= band_hi(i + 1, K))
-      acc = fma(NEG ? -E[i * C + j] : E[i * C + j], x[j], acc);
+    if (j >= band_lo(i + 1, K) && j <= band_hi(i + 1, K)) {
+      const T e = KIND == 0 ? c_Mp[off_patch(K) + i * C + j] : c_Kp[off_patch(K) + i * C + j];
+      acc = fma(NEG ? -e : e, x[j], acc);
+    }
   }
   return acc;
 }
 
-// FD transform along one axis, in place on a line of M = 2K-1 values at
-// stride s, using the mirror symmetry of the eigenvectors: modes 0..K-1 are
-// even (T[M-1-j][i] = T[j][i]), modes K..M-1 odd (T[M-1-j][i] = -T[j][i]).
-// forward (TRANSPOSE = true): y_i = sum_j T[j][i] x_j
-// backward:                   x_j = sum_i T[j][i] y_i
-template <int K, bool TRANSPOSE>
-__device__ __forceinline__ void fd_line(T* base, int s) {
+// FD transforms of one line of M = 2K-1 values held in registers, using the
+// mirror symmetry of the eigenvectors: modes 0..K-1 are even
+// (T[M-1-j][i] = T[j][i]), modes K..M-1 odd (T[M-1-j][i] = -T[j][i]).
+// forward: y_i = sum_j T[j][i] x_j;   backward: x_j = sum_i T[j][i] y_i
+template <int K>
+__device__ __forceinline__ void fd_forward(const T (&x)[2 * K - 1], T (&y)[2 * K - 1]) {
   constexpr int M = 2 * K - 1, c = K - 1;
-  const T* Tm = c_T + off_t(K);
-  if (TRANSPOSE) {
     T sv[K], dv[K > 1 ? K - 1 : 1];
 #pragma unroll
-    for (int j = 0; j < c; ++j) {
-      T a = base[j * s], b = base[(M - 1 - j) * s];
-      sv[j] = a + b;
-      dv[j] = a - b;
-    }
-    sv[c] = base[c * s];
+  for (int j = 0; j < c; ++j) {
+    sv[j] = x[j] + x[M - 1 - j];
+    dv[j] = x[j] - x[M - 1 - j];
+  }
+  sv[c] = x[c];
 #pragma unroll
-    for (int i = 0; i < K; ++i) {  // even modes
-      T acc = T(0);
+  for (int i = 0; i < K; ++i) {
+    T acc = T(0);
 #pragma unroll
-      for (int j = 0; j <= c; ++j) acc = fma(Tm[j * M + i], sv[j], acc);
-      base[i * s] = acc;
-    }
+    for (int j = 0; j <= c; ++j) acc = fma(c_T[off_t(K) + j * M + i], sv[j], acc);
+    y[i] = acc;
+  }
 #pragma unroll
-    for (int i = K; i < M; ++i) {  // odd modes
-      T acc = T(0);
+  for (int i = K; i < M; ++i) {
+    T acc = T(0);
 #pragma unroll
-      for (int j = 0; j < c; ++j) acc = fma(Tm[j * M + i], dv[j], acc);
-      base[i * s] = acc;
-    }
-  } else {
-    T y[M];
-#pragma unroll
-    for (int i = 0; i < M; ++i) y[i] = base[i * s];
-#pragma unroll
-    for (int j = 0; j < c; ++j) {
-      T e = T(0), o = T(0);
-#pragma unroll
-      for (int i = 0; i < K; ++i) e = fma(Tm[j * M + i], y[i], e);
-#pragma unroll
-      for (int i = K; i < M; ++i) o = fma(Tm[j * M + i], y[i], o);
-      base[j * s] = e + o;
-      base[(M - 1 - j) * s] = e - o;
-    }
-    T e = T(0);
-#pragma unroll
-    for (int i = 0; i < K; ++i) e = fma(Tm[c * M + i], y[i], e);
-    base[c * s] = e;
+    for (int j = 0; j < c; ++j) acc = fma(c_T[off_t(K) + j * M + i], dv[j], acc);
+    y[i] = acc;
   }
 }
 
-// Apply the FD transform along every axis of the M^DIM blocks of PPC patches
-// (block q at R + q * stride).
-template <int DIM, int K, bool TRANSPOSE, int NT, int PPC>
-__device__ __forceinline__ void fd_all_axes(T* R, int stride, const bool* valid) {
+template <int K>
+__device__ __forceinline__ void fd_backward(const T (&y)[2 * K - 1], T (&x)[2 * K - 1]) {
+  constexpr int M = 2 * K - 1, c = K - 1;
+  #pragma unroll
+  for (int j = 0; j < c; ++j) {
+    T e = T(0), o = T(0);
+#pragma unroll
+    for (int i = 0; i < K; ++i) e = fma(c_T[off_t(K) + j * M + i], y[i], e);
+#pragma unroll
+    for (int i = K; i < M; ++i) o = fma(c_T[off_t(K) + j * M + i], y[i], o);
+    x[j] = e + o;
+    x[M - 1 - j] = e - o;
+  }
+  T e = T(0);
+#pragma unroll
+  for (int i = 0; i < K; ++i) e = fma(c_T[off_t(K) + c * M + i], y[i], e);
+  x[c] = e;
+}
+
+// FD transform of a shared-memory line in place (stride s); with SCALE the
+// result is multiplied elementwise by d[0], d[ds], ... (the diagonal).
+template <int K, bool FORWARD, bool SCALE = false>
+__device__ __forceinline__ void fd_smem_line(T* base, int s, const T* __restrict__ d = nullptr,
+                                             int ds = 0) {
   constexpr int M = 2 * K - 1;
-  constexpr int L = DIM == 3 ? M * M : M;
+  T in[M], out[M];
 #pragma unroll
-  for (int axis = 0; axis < DIM; ++axis) {
-    for (int idx = threadIdx.x; idx < PPC * L; idx += NT) {
-      const int q = idx / L, l = idx % L;
-      if (!valid[q]) continue;
-      T* Rq = R + q * stride;
-      if (DIM == 2) {
-        if (axis == 0) fd_line<K, TRANSPOSE>(Rq + l * M, 1);
-        else fd_line<K, TRANSPOSE>(Rq + l, M);
-      } else {
-        if (axis == 0) fd_line<K, TRANSPOSE>(Rq + l * M, 1);
-        else if (axis == 1) fd_line<K, TRANSPOSE>(Rq + (l % M) + (l / M) * M * M, M);
-        else fd_line<K, TRANSPOSE>(Rq + l, M * M);
-      }
-    }
-    __syncthreads();
-  }
+  for (int j = 0; j < M; ++j) in[j] = base[j * s];
+  if (FORWARD) fd_forward<K>(in, out);
+  else fd_backward<K>(in, out);
+#pragma unroll
+  for (int j = 0; j < M; ++j) base[j * s] = SCALE ? out[j] * __ldg(d + j * ds) : out[j];
 }
 
-// One colour of the sweep: each CTA takes PPC consecutive patches of the
-// colour; every stage distributes the lines of all its patches over the
-// threads, so partial warps are rare.
-template <int DIM, int K, int NT, int PPC>
+// Asynchronous global -> shared copy of one element (cp.async, cached in L1),
+// and the group commit / wait of the copies issued by this thread.
+__device__ __forceinline__ void async_copy(T* smem_dst, const T* gmem_src) {
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(dst), "l"(gmem_src), "n"(sizeof(T)));
+}
+__device__ __forceinline__ void async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Shared-memory plan of the sweep kernel, per patch (elements):
+//   IN  (NBUF copies): closure of u (C^d), then interior of b (M^d)
+//   WA  3D: stage-y results A1, A2;  2D: stage-y results P, Q
+//   WB  3D: stage-z results P, Q, then r and the FD work;  2D: r and FD work
+// Stage x always reads WA and writes WB.
+template <int DIM, int K>
+struct SweepSmem {
+  static constexpr int C = 2 * K + 1, M = 2 * K - 1;
+  static constexpr int NCLO = DIM == 3 ? C * C * C : C * C;
+  static constexpr int NINT = DIM == 3 ? M * M * M : M * M;
+  static constexpr int IN = NCLO + NINT;
+  static constexpr int WA = DIM == 3 ? 2 * C * M * M : 2 * C * M;
+  static constexpr int WB = DIM == 3 ? cmax(2 * C * C * M, M * M * M) : M * M;
+  static constexpr int per_patch(int nbuf) { return nbuf * IN + WA + WB; }
+};
+
+// One colour of the sweep.  Persistent CTAs walk groups of PPC consecutive
+// patches of the colour.  With NBUF = 2, while a group is computed the next
+// group's closure of u and interior of b stream into the other input buffer
+// (cp.async), so global-memory latency overlaps the contractions; NBUF = 1 is
+// used when two buffers do not fit in shared memory.  Stages (3D; 2D drops
+// the z stages):
+//   z: P,Q | y: A1,A2 | x: r + forward FD along x | forward FD y |
+//   forward FD z, times the FD diagonal | backward FD z | backward FD y |
+//   backward FD x + scatter (u_new = u_old + omega d, u_old from the buffer)
+// Same-colour patches never write each other's closure, so the buffered
+// closure values are the values the gather (eq. "gather") reads.
+template <int DIM, int K, int NT, int PPC, int NBUF>
 __global__ void __launch_bounds__(NT) patch_colour_kernel(T* __restrict__ u, const T* __restrict__ b,
                                                           const T* __restrict__ dinv, PatchLaunch pl) {
-  using D = PatchDims<DIM, K>;
-  constexpr int C = D::C, M = D::M;
-  constexpr int STRIDE = D::SA + D::SB;  // elements of shared memory per patch
+  using Z = SweepSmem<DIM, K>;
+  constexpr int C = Z::C, M = Z::M;
+  constexpr int LINES = DIM == 3 ? M * M : M;  // interior lines per axis
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* const S = reinterpret_cast<T*>(smem_raw);
-  __shared__ long long s_origin[PPC];
-  __shared__ bool s_valid[PPC];
-  const T* Mp = c_Mp + off_patch(K);
-  const T* Kp = c_Kp + off_patch(K);
+  T* const IN0 = reinterpret_cast<T*>(smem_raw);       // [NBUF][PPC][IN]
+  T* const WA = IN0 + NBUF * PPC * Z::IN;              // [PPC][WA]
+  T* const WB = WA + PPC * Z::WA;                      // [PPC][WB]
+  __shared__ long long s_origin[2][PPC];
+  __shared__ int s_nvalid[2];
   const long long py = pl.g.py, pz = pl.g.pz;
   const T sb = (T)pl.sb;
   const T om = (T)pl.omega;
   const int ngroups = (pl.n_patches + PPC - 1) / PPC;
 
-  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-    if (threadIdx.x < PPC) {
+  // patch origins of a group (threads 0..PPC-1); callers follow with a barrier
+  auto set_origins = [&](int grp, int slot) {
+    const int nv = min(PPC, pl.n_patches - grp * PPC);
+    if (threadIdx.x == 0) s_nvalid[slot] = nv;
+    if (threadIdx.x < nv) {
       const int pid = grp * PPC + threadIdx.x;
-      const bool ok = pid < pl.n_patches;
-      int i0 = 0, i1 = 0, i2 = 0;
-      if (ok) {
-        i0 = pid % pl.count[0];
-        const int rest = pid / pl.count[0];
-        i1 = rest % pl.count[1];
-        i2 = DIM == 3 ? rest / pl.count[1] : 0;
-      }
+      const int i0 = pid % pl.count[0];
+      const int rest = pid / pl.count[0];
+      const int i1 = rest % pl.count[1];
+      const int i2 = DIM == 3 ? rest / pl.count[1] : 0;
       const long long o0 = (long long)(pl.first[0] + 2 * i0 - 1) * K;
       const long long o1 = (long long)(pl.first[1] + 2 * i1 - 1) * K;
       const long long o2 = DIM == 3 ? (long long)(pl.first[2] + 2 * i2 - 1) * K : 0;
-      s_origin[threadIdx.x] = o0 + py * o1 + pz * o2;
-      s_valid[threadIdx.x] = ok;
+      s_origin[slot][threadIdx.x] = o0 + py * o1 + pz * o2;
     }
-    __syncthreads();
+  };
+  // issue the copies of the group whose origins are in `slot` into input
+  // buffer `slot`, then commit them as one group
+  auto prefetch = [&](int slot) {
+    const int nv = s_nvalid[slot];
+    T* dst0 = IN0 + slot * PPC * Z::IN;
+    for (int idx = threadIdx.x; idx < nv * Z::NCLO; idx += NT) {  // closure of u, x fastest
+      const int q = idx / Z::NCLO, t = idx % Z::NCLO;
+      const int x = t % C, row = t / C;
+      const long long g = s_origin[slot][q] + x + py * (row % C) + (DIM == 3 ? pz * (row / C) : 0);
+      async_copy(dst0 + q * Z::IN + t, u + g);
+    }
+    for (int idx = threadIdx.x; idx < nv * Z::NINT; idx += NT) {  // interior of b
+      const int q = idx / Z::NINT, t = idx % Z::NINT;
+      const int x = t % M, row = t / M;
+      const long long g = s_origin[slot][q] + 1 + x + py * (row % M + 1) +
+                          (DIM == 3 ? pz * (row / M + 1) : 0);
+      async_copy(dst0 + q * Z::IN + Z::NCLO + t, b + g);
+    }
+    async_commit();
+  };
 
-    // ---- gather the closures (eq. "gather") ----
-    for (int idx = threadIdx.x; idx < PPC * D::NCLO; idx += NT) {
-      const int q = idx / D::NCLO, t = idx % D::NCLO;
-      if (!s_valid[q]) continue;
-      const int x = t % C, y = (t / C) % C, z = DIM == 3 ? t / (C * C) : 0;
-      S[q * STRIDE + t] = u[s_origin[q] + x + py * y + pz * z];
-    }
+  int grp = blockIdx.x;
+  if (NBUF == 2 && grp < ngroups) {
+    set_origins(grp, 0);
     __syncthreads();
+    prefetch(0);
+  }
+  for (int it = 0; grp < ngroups; grp += gridDim.x, ++it) {
+    const int cur = NBUF == 2 ? (it & 1) : 0;
+    if (NBUF == 1) {
+      set_origins(grp, 0);
+      __syncthreads();
+      prefetch(0);
+      async_wait<0>();
+    } else if (grp + (int)gridDim.x < ngroups) {
+      set_origins(grp + gridDim.x, cur ^ 1);
+      __syncthreads();
+      prefetch(cur ^ 1);
+      async_wait<1>();  // this thread's copies of the current group are done
+    } else {
+      async_wait<0>();
+    }
+    __syncthreads();  // ... and everybody's
+    const int nvalid = s_nvalid[cur];
+    const T* IN = IN0 + cur * PPC * Z::IN;
 
     if (DIM == 3) {
-      // ---- stage z: P = Mp_z u, Q = Kp_z u   (dims x:C, y:C, z:M, in B) ----
-      for (int idx = threadIdx.x; idx < PPC * C * C; idx += NT) {
+      // ---- stage z: P = Mp_z u, Q = Kp_z u   (dims x:C, y:C, z:M, in WB) ----
+      for (int idx = threadIdx.x; idx < nvalid * C * C; idx += NT) {
         const int q = idx / (C * C), l = idx % (C * C);
-        if (!s_valid[q]) continue;
-        const T* A = S + q * STRIDE;
-        T* B = S + q * STRIDE + D::SA;
+        const T* U = IN + q * Z::IN;
+        T* B = WB + q * Z::WB;
         T x[C];
 #pragma unroll
-        for (int j = 0; j < C; ++j) x[j] = A[l + j * C * C];
+        for (int j = 0; j < C; ++j) x[j] = U[l + j * C * C];
 #pragma unroll
         for (int i = 0; i < M; ++i) {
-          B[l + i * C * C] = patch_row<K>(Mp, i, x);
-          B[C * C * M + l + i * C * C] = patch_row<K>(Kp, i, x);
+          B[l + i * C * C] = patch_row<K, 0>(i, x);
+          B[C * C * M + l + i * C * C] = patch_row<K, 1>(i, x);
         }
       }
       __syncthreads();
-      // ---- stage y: A1 = Mp_y P, A2 = Kp_y P + Mp_y Q   (dims x:C, y:M, z:M, in A) ----
-      for (int idx = threadIdx.x; idx < PPC * C * M; idx += NT) {
+      // ---- stage y: A1 = Mp_y P, A2 = Kp_y P + Mp_y Q   (dims x:C, y:M, z:M, in WA) ----
+      for (int idx = threadIdx.x; idx < nvalid * C * M; idx += NT) {
         const int q = idx / (C * M), l = idx % (C * M);
-        if (!s_valid[q]) continue;
-        T* A = S + q * STRIDE;
-        const T* B = S + q * STRIDE + D::SA;
+        T* A = WA + q * Z::WA;
+        const T* B = WB + q * Z::WB;
         const int x0 = l % C, z = l / C;
         T p[C], r[C];
 #pragma unroll
@@ -236,94 +280,108 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(T* __restrict__ u, con
         }
 #pragma unroll
         for (int i = 0; i < M; ++i) {
-          A[x0 + i * C + z * C * M] = patch_row<K>(Mp, i, p);
-          A[C * M * M + x0 + i * C + z * C * M] = patch_row<K>(Mp, i, r, patch_row<K>(Kp, i, p));
-        }
-      }
-      __syncthreads();
-      // ---- stage x: r = sb b - (Kp_x A1 + Mp_x A2)   (dims M^3, into B) ----
-      for (int idx = threadIdx.x; idx < PPC * M * M; idx += NT) {
-        const int q = idx / (M * M), l = idx % (M * M);
-        if (!s_valid[q]) continue;
-        const T* A = S + q * STRIDE;
-        T* B = S + q * STRIDE + D::SA;
-        const int y = l % M, z = l / M;
-        T a1[C], a2[C];
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-          a1[j] = A[j + C * (y + M * z)];
-          a2[j] = A[C * M * M + j + C * (y + M * z)];
-        }
-        const long long row = s_origin[q] + 1 + py * (y + 1) + pz * (z + 1);
-#pragma unroll
-        for (int i = 0; i < M; ++i) {
-          T acc = sb * b[row + i];
-          acc = patch_row<K, true>(Kp, i, a1, acc);
-          B[i + M * l] = patch_row<K, true>(Mp, i, a2, acc);
+          A[x0 + i * C + z * C * M] = patch_row<K, 0>(i, p);
+          A[C * M * M + x0 + i * C + z * C * M] = patch_row<K, 0>(i, r, patch_row<K, 1>(i, p));
         }
       }
       __syncthreads();
     } else {
-      // ---- stage y: P = Mp_y u, Q = Kp_y u   (dims x:C, y:M, into B) ----
-      for (int idx = threadIdx.x; idx < PPC * C; idx += NT) {
+      // ---- stage y: P = Mp_y u, Q = Kp_y u   (dims x:C, y:M, in WA) ----
+      for (int idx = threadIdx.x; idx < nvalid * C; idx += NT) {
         const int q = idx / C, l = idx % C;
-        if (!s_valid[q]) continue;
-        const T* A = S + q * STRIDE;
-        T* B = S + q * STRIDE + D::SA;
+        const T* U = IN + q * Z::IN;
+        T* A = WA + q * Z::WA;
         T x[C];
 #pragma unroll
-        for (int j = 0; j < C; ++j) x[j] = A[l + j * C];
+        for (int j = 0; j < C; ++j) x[j] = U[l + j * C];
 #pragma unroll
         for (int i = 0; i < M; ++i) {
-          B[l + i * C] = patch_row<K>(Mp, i, x);
-          B[C * M + l + i * C] = patch_row<K>(Kp, i, x);
-        }
-      }
-      __syncthreads();
-      // ---- stage x: r = sb b - (Kp_x P + Mp_x Q)   (dims M^2, into A: the
-      // closure is consumed) ----
-      for (int idx = threadIdx.x; idx < PPC * M; idx += NT) {
-        const int q = idx / M, l = idx % M;
-        if (!s_valid[q]) continue;
-        T* A = S + q * STRIDE;
-        const T* B = S + q * STRIDE + D::SA;
-        T p[C], r[C];
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-          p[j] = B[j + C * l];
-          r[j] = B[C * M + j + C * l];
-        }
-        const long long row = s_origin[q] + 1 + py * (l + 1);
-#pragma unroll
-        for (int i = 0; i < M; ++i) {
-          T acc = sb * b[row + i];
-          acc = patch_row<K, true>(Kp, i, p, acc);
-          A[i + M * l] = patch_row<K, true>(Mp, i, r, acc);
+          A[l + i * C] = patch_row<K, 0>(i, x);
+          A[C * M + l + i * C] = patch_row<K, 1>(i, x);
         }
       }
       __syncthreads();
     }
 
-    // ---- local solve by fast diagonalisation, in place ----
-    T* R0 = DIM == 3 ? S + D::SA : S;  // r of patch 0 (3D: buffer B, 2D: buffer A)
-    fd_all_axes<DIM, K, true, NT, PPC>(R0, STRIDE, s_valid);
-    for (int idx = threadIdx.x; idx < PPC * D::NINT; idx += NT) {
-      const int q = idx / D::NINT, t = idx % D::NINT;
-      if (s_valid[q]) R0[q * STRIDE + t] *= dinv[t];
+    // ---- stage x: r = sb b - (Kp_x X1 + Mp_x X2) per interior line (X1, X2 =
+    // A1, A2 in 3D, P, Q in 2D, both in WA), then the forward FD transform
+    // along x in registers; result into WB ----
+    for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {
+      const int q = idx / LINES, l = idx % LINES;
+      constexpr int PLANE = DIM == 3 ? C * M * M : C * M;
+      const T* X = WA + q * Z::WA;
+      const T* Bq = IN + q * Z::IN + Z::NCLO;
+      T a1[C], a2[C];
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        a1[j] = X[j + C * l];
+        a2[j] = X[PLANE + j + C * l];
+      }
+      T r[M], y[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        T acc = sb * Bq[M * l + i];
+        acc = patch_row<K, 1, true>(i, a1, acc);
+        r[i] = patch_row<K, 0, true>(i, a2, acc);
+      }
+      fd_forward<K>(r, y);
+      T* R = WB + q * Z::WB + M * l;
+#pragma unroll
+      for (int i = 0; i < M; ++i) R[i] = y[i];
     }
     __syncthreads();
-    fd_all_axes<DIM, K, false, NT, PPC>(R0, STRIDE, s_valid);
 
-    // ---- scatter (eq. "scatter"): u_interior += omega d ----
-    for (int idx = threadIdx.x; idx < PPC * D::NINT; idx += NT) {
-      const int q = idx / D::NINT, t = idx % D::NINT;
-      if (!s_valid[q]) continue;
-      const int x = t % M, y = (t / M) % M;
-      long long g = s_origin[q] + (x + 1) + py * (y + 1);
-      if (DIM == 3) g += pz * (t / (M * M) + 1);
-      u[g] = fma(om, R0[q * STRIDE + t], u[g]);
+    // ---- local solve by fast diagonalisation (App. A.3), in place in WB ----
+    if (DIM == 3) {
+      for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // forward y
+        const int q = idx / LINES, l = idx % LINES;
+        fd_smem_line<K, true>(WB + q * Z::WB + (l % M) + (l / M) * M * M, M);
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // forward z, diagonal
+        const int q = idx / LINES, l = idx % LINES;
+        fd_smem_line<K, true, true>(WB + q * Z::WB + l, M * M, dinv + l, M * M);
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // backward z
+        const int q = idx / LINES, l = idx % LINES;
+        fd_smem_line<K, false>(WB + q * Z::WB + l, M * M);
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // backward y
+        const int q = idx / LINES, l = idx % LINES;
+        fd_smem_line<K, false>(WB + q * Z::WB + (l % M) + (l / M) * M * M, M);
+      }
+      __syncthreads();
+    } else {
+      for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // forward y, diagonal
+        const int q = idx / LINES, l = idx % LINES;
+        fd_smem_line<K, true, true>(WB + q * Z::WB + l, M, dinv + l, M);
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // backward y
+        const int q = idx / LINES, l = idx % LINES;
+        fd_smem_line<K, false>(WB + q * Z::WB + l, M);
+      }
+      __syncthreads();
     }
-    __syncthreads();  // shared buffers and s_origin are reused by the next group
+
+    // ---- backward FD along x and scatter (eq. "scatter") ----
+    for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {
+      const int q = idx / LINES, l = idx % LINES;
+      const T* R = WB + q * Z::WB + M * l;
+      const T* U = IN + q * Z::IN;
+      // interior line l of the patch: closure row (y+1, z+1), x = 1..M
+      const int cl = DIM == 3 ? (l % M + 1) * C + (l / M + 1) * C * C : (l + 1) * C;
+      T yv[M], d[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) yv[i] = R[i];
+      fd_backward<K>(yv, d);
+      const long long row = s_origin[cur][q] + 1 + py * (l % M + 1) + (DIM == 3 ? pz * (l / M + 1) : 0);
+#pragma unroll
+      for (int i = 0; i < M; ++i) u[row + i] = fma(om, d[i], U[cl + 1 + i]);
+    }
+    __syncthreads();  // buffers and origins are refilled / reused next iteration
   }
 }
 
@@ -333,18 +391,20 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(T* __restrict__ u, con
 // p == 0 (vertex) -> cell c-1 row K plus cell c row 0.
 // Tile inputs: nodes [(c0-1)K, (c0+BC)K] (EI per direction, zero outside the
 // lattice); outputs: nodes [c0 K, (c0+BC) K) (EO per direction).
-template <int K, int EI>
-__device__ __forceinline__ T cell_row(const T* E, int o, const T (&x)[EI]) {
+template <int K, int EI, int KIND>
+__device__ __forceinline__ T cell_row(int o, const T (&x)[EI]) {
+  // KIND 0: unit-cell mass, 1: unit-cell stiffness (direct __constant__ index)
+  auto E = [](int i) -> T { return KIND == 0 ? c_Mc[off_cell(K) + i] : c_Kc[off_cell(K) + i]; };
   const int p = o % K;
   T acc = T(0);
   if (p == 0) {
 #pragma unroll
-    for (int q = 0; q <= K; ++q) acc = fma(E[K * (K + 1) + q], x[o + q], acc);
+    for (int q = 0; q <= K; ++q) acc = fma(E(K * (K + 1) + q), x[o + q], acc);
 #pragma unroll
-    for (int q = 0; q <= K; ++q) acc = fma(E[q], x[o + K + q], acc);
+    for (int q = 0; q <= K; ++q) acc = fma(E(q), x[o + K + q], acc);
   } else {
 #pragma unroll
-    for (int q = 0; q <= K; ++q) acc = fma(E[p * (K + 1) + q], x[o - p + K + q], acc);
+    for (int q = 0; q <= K; ++q) acc = fma(E(p * (K + 1) + q), x[o - p + K + q], acc);
   }
   return acc;
 }
@@ -366,8 +426,6 @@ __global__ void __launch_bounds__(NT) apply_kernel(const T* __restrict__ xin, T*
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);
   T* B = A + D::SA;
-  const T* Mc = c_Mc + off_cell(K);
-  const T* Kc = c_Kc + off_cell(K);
   const int N = al.g.N, n = al.g.n;
   const long long py = al.g.py, pz = al.g.pz;
   const int tiles = (n + BC - 1) / BC;
@@ -394,8 +452,8 @@ __global__ void __launch_bounds__(NT) apply_kernel(const T* __restrict__ xin, T*
         for (int j = 0; j < EI; ++j) v[j] = A[l + j * EI * EI];
 #pragma unroll
         for (int o = 0; o < EO; ++o) {
-          B[l + o * EI * EI] = cell_row<K, EI>(Mc, o, v);
-          B[EI * EI * EO + l + o * EI * EI] = cell_row<K, EI>(Kc, o, v);
+          B[l + o * EI * EI] = cell_row<K, EI, 0>(o, v);
+          B[EI * EI * EO + l + o * EI * EI] = cell_row<K, EI, 1>(o, v);
         }
       }
       __syncthreads();
@@ -410,8 +468,8 @@ __global__ void __launch_bounds__(NT) apply_kernel(const T* __restrict__ xin, T*
         }
 #pragma unroll
         for (int o = 0; o < EO; ++o) {
-          A[x0 + o * EI + z * EI * EO] = cell_row<K, EI>(Mc, o, p);
-          A[EI * EO * EO + x0 + o * EI + z * EI * EO] = cell_row<K, EI>(Kc, o, p) + cell_row<K, EI>(Mc, o, q);
+          A[x0 + o * EI + z * EI * EO] = cell_row<K, EI, 0>(o, p);
+          A[EI * EO * EO + x0 + o * EI + z * EI * EO] = cell_row<K, EI, 1>(o, p) + cell_row<K, EI, 0>(o, q);
         }
       }
       __syncthreads();
@@ -431,7 +489,7 @@ __global__ void __launch_bounds__(NT) apply_kernel(const T* __restrict__ xin, T*
         for (int o = 0; o < EO; ++o) {
           int gx = g0 + K + o;
           if (gx <= 0 || gx >= N - 1) continue;
-          T v = alpha * (cell_row<K, EI>(Kc, o, a1) + cell_row<K, EI>(Mc, o, a2));
+          T v = alpha * (cell_row<K, EI, 1>(o, a1) + cell_row<K, EI, 0>(o, a2));
           if (bvec) v += beta * bvec[row + gx];
           y[row + gx] = v;
         }
@@ -444,8 +502,8 @@ __global__ void __launch_bounds__(NT) apply_kernel(const T* __restrict__ xin, T*
         for (int j = 0; j < EI; ++j) v[j] = A[l + j * EI];
 #pragma unroll
         for (int o = 0; o < EO; ++o) {
-          B[l + o * EI] = cell_row<K, EI>(Mc, o, v);
-          B[EI * EO + l + o * EI] = cell_row<K, EI>(Kc, o, v);
+          B[l + o * EI] = cell_row<K, EI, 0>(o, v);
+          B[EI * EO + l + o * EI] = cell_row<K, EI, 1>(o, v);
         }
       }
       __syncthreads();
@@ -463,7 +521,7 @@ __global__ void __launch_bounds__(NT) apply_kernel(const T* __restrict__ xin, T*
         for (int o = 0; o < EO; ++o) {
           int gx = g0 + K + o;
           if (gx <= 0 || gx >= N - 1) continue;
-          T v = alpha * (cell_row<K, EI>(Kc, o, p) + cell_row<K, EI>(Mc, o, q));
+          T v = alpha * (cell_row<K, EI, 1>(o, p) + cell_row<K, EI, 0>(o, q));
           if (bvec) v += beta * bvec[row + gx];
           y[row + gx] = v;
         }

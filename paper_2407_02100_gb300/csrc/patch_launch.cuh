@@ -11,17 +11,40 @@ namespace GMG_NS {
 
 constexpr int kApplyThreads = 128;
 
-// patches per CTA and threads per CTA of the sweep kernel: enough lines per
-// stage to fill whole warps, shared memory per CTA kept near 32-64 KB
-constexpr int sweep_ppc(int dim, int k) {
-  return dim == 2 ? 8 : (k <= 2 ? 8 : k <= 4 ? 4 : k <= 6 ? 2 : 1);
-}
-constexpr int sweep_threads(int dim, int k) { return dim == 3 && k >= 6 ? 256 : 128; }
+// Sweep kernel configuration: patches per CTA (enough interior lines per
+// stage to fill whole warps), threads, and double buffering of the inputs
+// whenever two input buffers fit in about half of the shared memory.
+template <int DIM, int K>
+struct SweepCfg {
+  // FP64 is bound by the FP64 pipe: many patches per CTA for full warps, one
+  // input buffer (occupancy hides the gather).  FP32 is bound by issue and
+  // latency: fewer patches per CTA, double-buffered inputs.
+  static constexpr bool F64 = sizeof(T) == 8;
+  static constexpr int PPC = DIM == 2 ? 8
+                           : F64 ? (K <= 2 ? 8 : K <= 4 ? 4 : K <= 6 ? 2 : 1)
+                                 : (K <= 2 ? 8 : K == 3 ? 4 : K == 4 ? 2 : 1);
+  static constexpr int NT = DIM == 3 && (K >= 6 || (F64 && K >= 3)) ? 256 : 128;
+  static constexpr int NBUF =
+      !F64 && PPC * SweepSmem<DIM, K>::per_patch(2) * (int)sizeof(T) <= 110 * 1024 ? 2 : 1;
+  static constexpr int SMEM = PPC * SweepSmem<DIM, K>::per_patch(NBUF) * (int)sizeof(T);
+  static_assert(SMEM <= 227 * 1024, "sweep kernel shared memory exceeds the per-CTA limit");
+};
 
 // cells per tile edge of the operator kernel
 constexpr int apply_bc(int dim, int k) {
   return dim == 3 ? (k == 1 ? 8 : k == 2 ? 4 : k <= 4 ? 2 : 1)
                   : (k == 1 ? 16 : k == 2 ? 8 : k <= 4 ? 4 : 2);
+}
+
+static int sm_count() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+      sms = 152;
+  }
+  return sms;
 }
 
 template <typename KernelT>
@@ -35,14 +58,19 @@ static int prepare(KernelT kern, int smem) {
 
 template <int DIM, int K>
 static int patch_impl(const PatchLaunch& pl, T* u, const T* b, const T* dinv, cudaStream_t s) {
-  using D = PatchDims<DIM, K>;
-  constexpr int PPC = sweep_ppc(DIM, K), NT = sweep_threads(DIM, K);
-  constexpr int SMEM = PPC * D::SMEM_BYTES;
-  auto kern = patch_colour_kernel<DIM, K, NT, PPC>;
-  if (prepare(kern, SMEM) != GMG_OK) return GMG_ERR_CUDA;
+  using Cfg = SweepCfg<DIM, K>;
+  auto kern = patch_colour_kernel<DIM, K, Cfg::NT, Cfg::PPC, Cfg::NBUF>;
+  static int per_sm = 0;  // resident CTAs per SM (persistent grid)
+  if (per_sm == 0) {
+    if (prepare(kern, Cfg::SMEM) != GMG_OK) return GMG_ERR_CUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::NT, Cfg::SMEM) != cudaSuccess ||
+        per_sm <= 0)
+      return GMG_ERR_CUDA;
+  }
   if (pl.n_patches <= 0) return GMG_OK;
-  int grid = std::min((pl.n_patches + PPC - 1) / PPC, 1 << 30);
-  kern<<<grid, NT, SMEM, s>>>(u, b, dinv, pl);
+  const int ngroups = (pl.n_patches + Cfg::PPC - 1) / Cfg::PPC;
+  const int grid = std::min(ngroups, per_sm * sm_count());
+  kern<<<grid, Cfg::NT, Cfg::SMEM, s>>>(u, b, dinv, pl);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
 }
