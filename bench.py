@@ -43,6 +43,21 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 CPU_SAMPLE = dict(dim=3, degree=4, n_cells=8, n_levels=3)
 
 
+def max_over_ranks(value, dist=None, device="cpu"):
+    """Largest value over all ranks (the job time is the slowest rank's)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(nodes_per_rank, world_size, steps, max_ms):
+    """Whole-job throughput in MDoF/s: nodes solved by all ranks / job time."""
+    return nodes_per_rank * world_size * steps / (max_ms * 1e-3) / 1e6
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -225,13 +240,9 @@ def run_ours(args):
         torch.cuda.synchronize()
     barrier()
     launches = gmg.gmg_kernel_launch_count() - launches0
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     ms_per_step = ms / args.steps
-    value = nodes * ws * args.steps / (ms * 1e-3) / 1e6
+    value = whole_job_rate(nodes, ws, args.steps, ms)
 
     # ---- dominant kernel: the finest-level patch sweep (8 colour launches) ----
     us = P.zeros(dtype=torch.float64)
@@ -267,12 +278,8 @@ def run_ours(args):
         gmg.cg_gmg_solve(P.h, u, b_e2e, RTOL, 100)
         u_pin.copy_(u, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = nodes * ws / e2e_s / 1e6
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, "cuda")
+    e2e_value = whole_job_rate(nodes, ws, 1, e2e_s * 1e3)
 
     # ---- parity of the final solution (residual computed on the device by the
     # library's FP64 operator, norm by torch) ----
