@@ -51,6 +51,12 @@ enum gmg_precision {
   GMG_FP32 = 1   /* smoother, transfer and V-cycle in float (inside FP64 CG) */
 };
 
+enum gmg_sweep_variant {
+  GMG_SWEEP_COMBINED = 0,   /* Algorithm 4: combined colourised (local residuals) */
+  GMG_SWEEP_SEPARATED = 1,  /* Algorithm 3: global residual per colour, then solves */
+  GMG_SWEEP_BATCHED = 2     /* Algorithm 5: Z-curve batches of n_B patches per colour */
+};
+
 typedef struct gmg_problem gmg_problem; /* opaque; owns all level data */
 
 typedef struct {
@@ -123,6 +129,20 @@ int gmg_smooth(gmg_problem* p, int level, void* u, const void* b, int n_sweeps, 
 /* One colour of the smoother (all patches of colour `colour`, 0..2^dim-1),
  * in place on u.  Same arguments and semantics as gmg_smooth. */
 int gmg_smooth_colour(gmg_problem* p, int level, void* u, const void* b, int colour);
+
+/* One smoothing step on `level` in one of the paper's loop organisations
+ * (Sec. 3.2, 3.3 and 4.1): GMG_SWEEP_COMBINED = Algorithm 4 (as gmg_smooth);
+ * GMG_SWEEP_SEPARATED = Algorithm 3, per colour one level residual
+ * r = b - A u followed by the colour's local solves from r (same result as
+ * Algorithm 4 up to rounding); GMG_SWEEP_BATCHED = Algorithm 5, patches in
+ * Z-curve order (Morton order of the vertex index, v_0 lowest bit) grouped by
+ * colour and cut into batches of batch_size; for each batch index every
+ * colour's batch in turn (equals Algorithm 4 when batch_size >= the largest
+ * colour).  reverse != 0 reverses colours (and batches).  The first batched
+ * call on a level allocates its patch list.  Errors: INVALID_ARG (unknown
+ * variant, batch_size < 1), OOM, CUDA. */
+int gmg_smooth_variant(gmg_problem* p, int level, void* u, const void* b, int variant,
+                       long long batch_size, int reverse);
 
 /* coarse = R fine with R = P^T, the transpose of the embedding prolongation
  * (Sec. 2, restriction as the adjoint of the embedding).  fine: level

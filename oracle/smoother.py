@@ -110,3 +110,60 @@ def colour_sorted_vertices(mesh: Mesh, reverse=False):
     if reverse:
         order = reversed(list(order))
     return np.concatenate([mesh.vertices_of_colour(c) for c in order], axis=0)
+
+
+def morton_key(v):
+    """Z-curve (Morton) key of vertex multi-indices v [..., dim]: the bits of
+    v_0, v_1 (, v_2) interleaved, v_0 in the lowest position (Sec. 4.1 step 1
+    orders patches along a Z-curve; our reading: the Morton order of the
+    vertex index)."""
+    v = np.asarray(v, dtype=np.int64)
+    dim = v.shape[-1]
+    key = np.zeros(v.shape[:-1], dtype=np.int64)
+    for bit in range(20):
+        for a in range(dim):
+            key |= ((v[..., a] >> bit) & 1) << (dim * bit + a)
+    return key
+
+
+def batches_alg5(mesh: Mesh, n_b):
+    """Sec. 4.1 set-up: (1) all patches in Z-curve order, (2) grouped by
+    colour keeping that order, (3) each colour split into batches of n_b.
+    Returns P[b][k] = vertex arrays (possibly empty)."""
+    V = mesh.vertices()
+    V = V[np.argsort(morton_key(V), kind="stable")]
+    col = mesh.colour(V)
+    per_colour = [V[col == k] for k in range(mesh.n_colours)]
+    nb = max((len(P) + n_b - 1) // n_b for P in per_colour) if len(V) else 0
+    return [[P[b * n_b:(b + 1) * n_b] for P in per_colour] for b in range(nb)]
+
+
+def sweep_alg5(smoother: PatchSmoother, u, b, n_b):
+    """Algorithm 5: for each batch b, for each colour k, all patches of
+    P_{b,k} (independent: one colour) updated from the current state."""
+    u = np.array(u, dtype=np.float64, copy=True)
+    m = smoother.mesh
+    for batch in batches_alg5(m, n_b):
+        for P in batch:
+            if len(P) == 0:
+                continue
+            r = smoother.local_residual(u, b, P)
+            d = smoother.local_solve(r)
+            u[m.interior_index(P).ravel()] += smoother.omega * d.ravel()
+    return u
+
+
+def sweep_alg3(mesh: Mesh, A, smoother: PatchSmoother, u, b, reverse=False):
+    """Algorithm 3 (separated, colourised): per colour, one global residual
+    r = b - A u with the assembled matrix, then every local solve of the
+    colour from r."""
+    u = np.array(u, dtype=np.float64, copy=True)
+    for c in smoother.colour_order(reverse):
+        r = b - A @ u
+        V = mesh.vertices_of_colour(c)
+        if len(V) == 0:
+            continue
+        inn = mesh.interior_index(V)
+        d = smoother.local_solve(r[inn])
+        u[inn.ravel()] += smoother.omega * d.ravel()
+    return u

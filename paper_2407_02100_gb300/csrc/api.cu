@@ -4,6 +4,7 @@
 // only builds tables on the host, owns device buffers and sequences launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -29,6 +30,9 @@ struct Level {
   void* u = nullptr;  // level correction (problem precision)
   void* b = nullptr;  // level right-hand side (problem precision)
   void* r = nullptr;  // level residual (problem precision)
+  // patches of every colour in Z-curve order (Algorithm 5), built on demand
+  int* zlist = nullptr;
+  int zoff[9] = {0};
 };
 
 }  // namespace
@@ -131,12 +135,13 @@ int apply_level(gmg_problem* p, int level, const void* x, void* y, const void* b
 
 double op_scale(const Level& L) { return L.g.dim == 3 ? L.h : 1.0; }  // h^{d-2}
 
-int smooth_colour(gmg_problem* p, int level, void* u, const void* b, int colour) {
-  const Level& L = p->levels[level];
+PatchLaunch colour_launch(const Level& L, int colour, double omega) {
   const int dim = L.g.dim, n = L.g.n;
   PatchLaunch pl;
   pl.g = L.g;
   pl.n_patches = 1;
+  pl.plist = nullptr;
+  pl.mode = 0;
   for (int a = 0; a < 3; ++a) {
     if (a < dim) {
       bool odd = (colour >> a) & 1;
@@ -149,17 +154,108 @@ int smooth_colour(gmg_problem* p, int level, void* u, const void* b, int colour)
     pl.n_patches *= pl.count[a];
   }
   pl.sb = dim == 3 ? 1.0 / L.h : 1.0;
-  pl.omega = p->desc.damping;
+  pl.omega = omega;
+  return pl;
+}
+
+int launch_colour(gmg_problem* p, const PatchLaunch& pl, void* u, const void* b) {
   if (pl.n_patches == 0) return GMG_OK;
   if (p->esize == 8)
     return launch_patch_colour<double>(pl, (double*)u, (const double*)b, (const double*)p->dinv, p->stream);
   return launch_patch_colour<float>(pl, (float*)u, (const float*)b, (const float*)p->dinv, p->stream);
 }
 
+int smooth_colour(gmg_problem* p, int level, void* u, const void* b, int colour) {
+  return launch_colour(p, colour_launch(p->levels[level], colour, p->desc.damping), u, b);
+}
+
 int smooth(gmg_problem* p, int level, void* u, const void* b, int n_sweeps, int reverse) {
   const int nc = 1 << p->levels[level].g.dim;
   for (int s = 0; s < n_sweeps; ++s)
     for (int i = 0; i < nc; ++i) CHECK(smooth_colour(p, level, u, b, reverse ? nc - 1 - i : i));
+  return GMG_OK;
+}
+
+// Z-curve (Morton) key of a vertex: bits of v_0, v_1 (, v_2) interleaved,
+// v_0 lowest (Sec. 4.1 step 1).
+unsigned long long morton(int dim, const int v[3]) {
+  unsigned long long key = 0;
+  for (int bit = 0; bit < 20; ++bit)
+    for (int a = 0; a < dim; ++a)
+      key |= (unsigned long long)((v[a] >> bit) & 1) << (dim * bit + a);
+  return key;
+}
+
+// Patches of every colour sorted along the Z-curve (Sec. 4.1 steps 1-2),
+// as lexicographic ids within the colour; built once per level.
+int build_zlists(gmg_problem* p, int level) {
+  Level& L = p->levels[level];
+  if (L.zlist) return GMG_OK;
+  const int nc = 1 << L.g.dim;
+  std::vector<int> all;
+  for (int c = 0; c < nc; ++c) {
+    PatchLaunch pl = colour_launch(L, c, 1.0);
+    std::vector<std::pair<unsigned long long, int>> keyed(pl.n_patches);
+    for (int pid = 0; pid < pl.n_patches; ++pid) {
+      int rest = pid, v[3] = {0, 0, 0};
+      for (int a = 0; a < L.g.dim; ++a) {
+        v[a] = pl.first[a] + 2 * (rest % pl.count[a]);
+        rest /= pl.count[a];
+      }
+      keyed[pid] = {morton(L.g.dim, v), pid};
+    }
+    std::stable_sort(keyed.begin(), keyed.end(),
+                     [](const auto& x, const auto& y) { return x.first < y.first; });
+    L.zoff[c] = (int)all.size();
+    for (const auto& kv : keyed) all.push_back(kv.second);
+  }
+  L.zoff[nc] = (int)all.size();
+  void* d = nullptr;
+  CHECK(dalloc(p, &d, std::max<size_t>(all.size(), 1) * sizeof(int)));
+  if (!all.empty() &&
+      cudaMemcpy(d, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+    return GMG_ERR_CUDA;
+  L.zlist = static_cast<int*>(d);
+  return GMG_OK;
+}
+
+// Algorithm 3: per colour, r = b - A u on the whole level, then the local
+// solves of the colour from r (solve-only kernel mode).
+int smooth_separated(gmg_problem* p, int level, void* u, const void* b, int reverse) {
+  Level& L = p->levels[level];
+  const int nc = 1 << L.g.dim;
+  for (int i = 0; i < nc; ++i) {
+    const int c = reverse ? nc - 1 - i : i;
+    CHECK(apply_level(p, level, u, L.r, b, -op_scale(L), 1.0));
+    PatchLaunch pl = colour_launch(L, c, p->desc.damping);
+    pl.mode = 1;
+    CHECK(launch_colour(p, pl, u, L.r));
+  }
+  return GMG_OK;
+}
+
+// Algorithm 5: batches of n_b patches per colour in Z-curve order; for each
+// batch index, every colour's batch in turn.
+int smooth_batched(gmg_problem* p, int level, void* u, const void* b, long long n_b, int reverse) {
+  CHECK(build_zlists(p, level));
+  Level& L = p->levels[level];
+  const int nc = 1 << L.g.dim;
+  long long nbatch = 0;
+  for (int c = 0; c < nc; ++c)
+    nbatch = std::max(nbatch, ((long long)(L.zoff[c + 1] - L.zoff[c]) + n_b - 1) / n_b);
+  for (long long bi = 0; bi < nbatch; ++bi) {
+    const long long bb = reverse ? nbatch - 1 - bi : bi;
+    for (int i = 0; i < nc; ++i) {
+      const int c = reverse ? nc - 1 - i : i;
+      const long long size = L.zoff[c + 1] - L.zoff[c];
+      const long long s0 = bb * n_b, s1 = std::min(size, s0 + n_b);
+      if (s0 >= s1) continue;
+      PatchLaunch pl = colour_launch(L, c, p->desc.damping);
+      pl.plist = L.zlist + L.zoff[c] + s0;
+      pl.n_patches = (int)(s1 - s0);
+      CHECK(launch_colour(p, pl, u, b));
+    }
+  }
   return GMG_OK;
 }
 
@@ -533,6 +629,19 @@ int gmg_smooth_colour(gmg_problem* p, int level, void* u, const void* b, int col
   if (!valid_level(p, level) || !u || !b || u == b) return GMG_ERR_INVALID_ARG;
   if (colour < 0 || colour >= (1 << p->levels[level].g.dim)) return GMG_ERR_INVALID_ARG;
   return smooth_colour(p, level, u, b, colour);
+}
+
+int gmg_smooth_variant(gmg_problem* p, int level, void* u, const void* b, int variant,
+                       long long batch_size, int reverse) {
+  if (!valid_level(p, level) || !u || !b || u == b) return GMG_ERR_INVALID_ARG;
+  switch (variant) {
+    case GMG_SWEEP_COMBINED: return smooth(p, level, u, b, 1, reverse);
+    case GMG_SWEEP_SEPARATED: return smooth_separated(p, level, u, b, reverse);
+    case GMG_SWEEP_BATCHED:
+      if (batch_size < 1) return GMG_ERR_INVALID_ARG;
+      return smooth_batched(p, level, u, b, batch_size, reverse);
+    default: return GMG_ERR_INVALID_ARG;
+  }
 }
 
 int gmg_restrict(gmg_problem* p, int fine_level, const void* fine, void* coarse) {

@@ -26,6 +26,12 @@ struct PatchLaunch {
   int n_patches;
   double sb;          // h^{2-d}: scales b to the unit-cell operator
   double omega;       // damping of the scatter
+  // optional list of patches (lexicographic ids within the colour); patch
+  // number i of the launch is plist[i] when plist != nullptr
+  const int* plist;
+  // 0: combined local residual + solve (Algorithm 4);
+  // 1: solve only, b holds the global residual r = b - A u (Algorithm 3)
+  int mode;
 };
 
 // y = alpha * (A_ref x) + beta * bvec on owned interior nodes, where A_ref is

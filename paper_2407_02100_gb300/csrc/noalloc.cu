@@ -98,6 +98,8 @@ extern "C" int gmg_smooth_noalloc(int dim, int degree, int n_cells, double dampi
   pl.g.pz = (long long)pl.g.py * pl.g.N;
   pl.sb = dim == 3 ? (double)n_cells : 1.0;  // h^{2-d}
   pl.omega = damping;
+  pl.plist = nullptr;
+  pl.mode = 0;
   const int nc = 1 << dim;
   for (int sweep = 0; sweep < n_sweeps; ++sweep) {
     for (int i = 0; i < nc; ++i) {

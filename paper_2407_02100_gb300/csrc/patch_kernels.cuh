@@ -193,7 +193,8 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(T* __restrict__ u, con
     const int nv = min(PPC, pl.n_patches - grp * PPC);
     if (threadIdx.x == 0) s_nvalid[slot] = nv;
     if (threadIdx.x < nv) {
-      const int pid = grp * PPC + threadIdx.x;
+      int pid = grp * PPC + threadIdx.x;
+      if (pl.plist) pid = pl.plist[pid];
       const int i0 = pid % pl.count[0];
       const int rest = pid / pl.count[0];
       const int i1 = rest % pl.count[1];
@@ -209,7 +210,8 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(T* __restrict__ u, con
   auto prefetch = [&](int slot) {
     const int nv = s_nvalid[slot];
     T* dst0 = IN0 + slot * PPC * Z::IN;
-    for (int idx = threadIdx.x; idx < nv * Z::NCLO; idx += NT) {  // closure of u, x fastest
+    // the solve-only mode needs no closure: only the residual's interior
+    for (int idx = threadIdx.x; idx < (pl.mode == 0 ? nv * Z::NCLO : 0); idx += NT) {  // closure of u
       const int q = idx / Z::NCLO, t = idx % Z::NCLO;
       const int x = t % C, row = t / C;
       const long long g = s_origin[slot][q] + x + py * (row % C) + (DIM == 3 ? pz * (row / C) : 0);
@@ -250,7 +252,9 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(T* __restrict__ u, con
     const int nvalid = s_nvalid[cur];
     const T* IN = IN0 + cur * PPC * Z::IN;
 
-    if (DIM == 3) {
+    if (pl.mode != 0) {
+      // solve only: nothing to evaluate, the buffer holds the residual
+    } else if (DIM == 3) {
       // ---- stage z: P = Mp_z u, Q = Kp_z u   (dims x:C, y:C, z:M, in WB) ----
       for (int idx = threadIdx.x; idx < nvalid * C * C; idx += NT) {
         const int q = idx / (C * C), l = idx % (C * C);
@@ -311,18 +315,23 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(T* __restrict__ u, con
       constexpr int PLANE = DIM == 3 ? C * M * M : C * M;
       const T* X = WA + q * Z::WA;
       const T* Bq = IN + q * Z::IN + Z::NCLO;
-      T a1[C], a2[C];
-#pragma unroll
-      for (int j = 0; j < C; ++j) {
-        a1[j] = X[j + C * l];
-        a2[j] = X[PLANE + j + C * l];
-      }
       T r[M], y[M];
+      if (pl.mode == 0) {
+        T a1[C], a2[C];
 #pragma unroll
-      for (int i = 0; i < M; ++i) {
-        T acc = sb * Bq[M * l + i];
-        acc = patch_row<K, 1, true>(i, a1, acc);
-        r[i] = patch_row<K, 0, true>(i, a2, acc);
+        for (int j = 0; j < C; ++j) {
+          a1[j] = X[j + C * l];
+          a2[j] = X[PLANE + j + C * l];
+        }
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+          T acc = sb * Bq[M * l + i];
+          acc = patch_row<K, 1, true>(i, a1, acc);
+          r[i] = patch_row<K, 0, true>(i, a2, acc);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < M; ++i) r[i] = sb * Bq[M * l + i];
       }
       fd_forward<K>(r, y);
       T* R = WB + q * Z::WB + M * l;
@@ -379,7 +388,8 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(T* __restrict__ u, con
       fd_backward<K>(yv, d);
       const long long row = s_origin[cur][q] + 1 + py * (l % M + 1) + (DIM == 3 ? pz * (l / M + 1) : 0);
 #pragma unroll
-      for (int i = 0; i < M; ++i) u[row + i] = fma(om, d[i], U[cl + 1 + i]);
+      for (int i = 0; i < M; ++i)
+        u[row + i] = fma(om, d[i], pl.mode == 0 ? U[cl + 1 + i] : u[row + i]);
     }
     __syncthreads();  // buffers and origins are refilled / reused next iteration
   }

@@ -27,7 +27,8 @@ EXPORTS = ["gmg_create", "gmg_destroy", "gmg_vector_layout", "gmg_level_info",
            "gmg_apply_operator", "gmg_apply_operator_f64", "gmg_smooth", "gmg_smooth_colour",
            "gmg_restrict", "gmg_prolongate_add", "gmg_coarse_solve", "gmg_vcycle",
            "cg_gmg_solve", "gmg_patch_fd_1d", "gmg_kernel_launch_count", "gmg_status_string",
-           "gmg_smooth_noalloc"]
+           "gmg_smooth_noalloc", "gmg_smooth_variant"]
+GMG_SWEEP_COMBINED, GMG_SWEEP_SEPARATED, GMG_SWEEP_BATCHED = 0, 1, 2
 
 
 class GmgDesc(ctypes.Structure):
@@ -70,6 +71,7 @@ def lib():
             "gmg_apply_operator_f64": [vp, i, vp, vp],
             "gmg_smooth": [vp, i, vp, vp, i, i],
             "gmg_smooth_colour": [vp, i, vp, vp, i],
+            "gmg_smooth_variant": [vp, i, vp, vp, i, ll, i],
             "gmg_restrict": [vp, i, vp, vp],
             "gmg_prolongate_add": [vp, i, vp, vp],
             "gmg_coarse_solve": [vp, vp, vp],
@@ -144,6 +146,11 @@ def gmg_smooth(h, level, u, b, n_sweeps=1, reverse=False):
 
 def gmg_smooth_colour(h, level, u, b, colour):
     _check("gmg_smooth_colour", lib().gmg_smooth_colour(h, level, _ptr(u), _ptr(b), colour))
+
+
+def gmg_smooth_variant(h, level, u, b, variant, batch_size=1, reverse=False):
+    _check("gmg_smooth_variant", lib().gmg_smooth_variant(h, level, _ptr(u), _ptr(b), variant,
+                                                          batch_size, int(bool(reverse))))
 
 
 def gmg_restrict(h, fine_level, fine, coarse):

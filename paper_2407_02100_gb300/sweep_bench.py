@@ -25,6 +25,9 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--sweeps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--variant", choices=["combined", "separated", "batched"], default="combined",
+                    help="Algorithm 4, 3 or 5 of the paper")
+    ap.add_argument("--batch", type=int, default=32768, help="n_B of Algorithm 5")
     a = ap.parse_args()
     build.build()
     prec = gmg.GMG_FP64 if a.precision == "fp64" else gmg.GMG_FP32
@@ -45,10 +48,13 @@ def main():
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps * 1e-3
 
-    t_sweep = timed(lambda: gmg.gmg_smooth(P.h, 0, u, b, 1, False), a.sweeps)
+    variant = {"combined": gmg.GMG_SWEEP_COMBINED, "separated": gmg.GMG_SWEEP_SEPARATED,
+               "batched": gmg.GMG_SWEEP_BATCHED}[a.variant]
+    t_sweep = timed(lambda: gmg.gmg_smooth_variant(P.h, 0, u, b, variant, a.batch, False), a.sweeps)
     t_apply = timed(lambda: gmg.gmg_apply_operator(P.h, 0, u, y), a.sweeps)
     nodes = (a.n * a.degree + 1) ** a.dim
     print(json.dumps({"dim": a.dim, "degree": a.degree, "n_cells": a.n, "precision": a.precision,
+                      "variant": a.variant, "batch": a.batch if a.variant == "batched" else None,
                       "nodes": nodes, "sweep_ms": t_sweep * 1e3, "sweep_mdofs": nodes / t_sweep / 1e6,
                       "apply_ms": t_apply * 1e3, "apply_mdofs": nodes / t_apply / 1e6}))
     P.close()

@@ -6,8 +6,8 @@ import numpy as np
 import pytest
 
 from oracle.mesh import Mesh
-from oracle.smoother import (PatchSmoother, colour_sorted_vertices, sweep_alg1,
-                             sweep_alg2)
+from oracle.smoother import (PatchSmoother, batches_alg5, colour_sorted_vertices,
+                             morton_key, sweep_alg1, sweep_alg2, sweep_alg3, sweep_alg5)
 from paper_2407_02100_gb300 import inputs
 
 
@@ -157,3 +157,43 @@ def test_exact_local_solve_forgets_old_interior():
     a = sweep_alg2(s, u, b, v)
     c = sweep_alg2(s, u2, b, v)
     np.testing.assert_allclose(a, c, rtol=0, atol=1e-12 * np.abs(a).max())
+
+
+def test_morton_key_small_cases():
+    """Bit interleaving: (1,0)->1, (0,1)->2, (1,1)->3, (2,0)->4, (3,5)->0b100111."""
+    got = morton_key(np.array([[1, 0], [0, 1], [1, 1], [2, 0], [3, 5]]))
+    np.testing.assert_array_equal(got, [1, 2, 3, 4, 0b100111])
+    assert morton_key(np.array([[1, 1, 1]]))[0] == 7
+
+
+@pytest.mark.parametrize("dim,k,n", [(2, 2, 6), (3, 2, 5)])
+def test_algorithm3_equals_algorithm4(dim, k, n):
+    """Sec. 3.3: the separated and the combined colourised smoothers are the
+    same mathematical algorithm."""
+    m = Mesh(dim, k, n)
+    A = m.assemble()
+    s = PatchSmoother(m)
+    u0, b = _rand(m, 15), _rand(m, 16)
+    for rev in (False, True):
+        np.testing.assert_allclose(sweep_alg3(m, A, s, u0, b, rev), s.sweep(u0, b, rev),
+                                   rtol=0, atol=1e-12 * np.abs(b).max())
+
+
+@pytest.mark.parametrize("dim,k,n", [(2, 2, 7), (3, 1, 6)])
+def test_algorithm5_limits(dim, k, n):
+    """n_B >= colour size gives Algorithm 4; n_B = 1 gives the sequential loop
+    (Algorithm 2, and Algorithm 1 with global residuals) over the interleaved
+    sequence batch 0 colours 0..2^d-1, batch 1 colours 0..2^d-1, ..."""
+    m = Mesh(dim, k, n)
+    A = m.assemble()
+    s = PatchSmoother(m)
+    u0, b = _rand(m, 17), _rand(m, 18)
+    big = len(m.vertices())
+    np.testing.assert_allclose(sweep_alg5(s, u0, b, big), s.sweep(u0, b), rtol=0, atol=1e-13)
+    seq = np.concatenate([P for batch in batches_alg5(m, 1) for P in batch if len(P)])
+    assert len(seq) == big and len({tuple(v) for v in seq}) == big
+    ref1 = sweep_alg1(m, A, u0, b, seq)
+    np.testing.assert_allclose(sweep_alg5(s, u0, b, 1), ref1, rtol=0, atol=1e-12 * np.abs(ref1).max())
+    np.testing.assert_allclose(sweep_alg2(s, u0, b, seq), ref1, rtol=0, atol=1e-12 * np.abs(ref1).max())
+    # a middle batch size differs from Algorithm 4 (the order matters)
+    assert np.abs(sweep_alg5(s, u0, b, 3) - s.sweep(u0, b)).max() > 1e-8
