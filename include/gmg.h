@@ -191,6 +191,61 @@ int cg_gmg_solve(gmg_problem* p, double* u, const double* b, double rtol, int ma
 int gmg_smooth_noalloc(int dim, int degree, int n_cells, double damping, double* u,
                        const double* b, int n_sweeps, int reverse, void* stream);
 
+/* ---- Batches of independent problems ------------------------------------
+ * Many problems of one dimension, degree and precision but different mesh
+ * sizes, solved together (each problem is the same method as a single
+ * gmg_problem; batching only schedules the work): one sweep-kernel launch per
+ * colour covers the patches of all problems at a given depth of their level
+ * hierarchies, the batched V-cycle is captured once into a CUDA graph and
+ * replayed, and the FP64 CG keeps per-problem scalars, stopping each problem
+ * when it converges.  Batch vectors concatenate the finest-level vectors of
+ * all problems: problem i occupies elements [offset_i, offset_i + n_elems_i)
+ * in its own gmg_vector_layout, gaps are zero. */
+typedef struct gmg_batch gmg_batch;
+
+/* desc: dim, degree, precision, damping, sweeps and stream shared by all
+ * problems (desc->n_cells and n_levels are ignored); n_cells[i] is problem
+ * i's finest mesh, levels by halving while even and >= 2.  Errors:
+ * INVALID_ARG (any problem's descriptor invalid, n_problems < 1), OOM, CUDA. */
+int gmg_batch_create(const gmg_desc* desc, int n_problems, const int* n_cells, gmg_batch** out);
+int gmg_batch_destroy(gmg_batch* b);
+
+/* Offset and length (elements) of problem i in a batch vector, and the
+ * batch vector length.  Host-only; outputs may be NULL. */
+int gmg_batch_layout(const gmg_batch* b, int problem, long long* offset, long long* n_elems,
+                     long long* total);
+
+/* The problem object of batch member i (owned by the batch: do not destroy;
+ * use it for gmg_vector_layout and single-problem calls on its own vectors). */
+int gmg_batch_problem(const gmg_batch* b, int problem, gmg_problem** out);
+
+/* One finest-level smoothing step (Algorithm 4) of every problem, in place on
+ * the batch vector u with right-hand side b (problem precision), one launch
+ * per colour; reverse != 0 takes the colours in descending order. */
+int gmg_batch_smooth(gmg_batch* b, void* u, const void* rhs, int reverse);
+
+/* x = V(rhs) for every problem (batch vectors, problem precision), through
+ * the captured CUDA graph (the first call captures it; make it before any
+ * capture of your own). */
+int gmg_batch_vcycle(gmg_batch* b, void* x, const void* rhs);
+
+/* PCG of every problem to ||r_i|| <= rtol ||b_i||, FP64 batch vectors u
+ * (initial guess in, solution out) and rhs.  iterations[i], rel_residual[i]
+ * (host arrays of n_problems entries, may be NULL) receive per-problem
+ * results.  Errors: INVALID_ARG, CUDA, NONFINITE, BREAKDOWN, NOT_CONVERGED. */
+int gmg_batch_cg_solve(gmg_batch* b, double* u, const double* rhs, double rtol, int max_it,
+                       int* iterations, double* rel_residual);
+
+/* Choose, by timing batched sweeps on the GPU, the number of patches per CTA
+ * of the batched sweep kernel (0 = the default configuration, or 1, 2, 4;
+ * the variants exist for 3D FP32 up to degree 4).  The choice never changes
+ * results: every patch is computed the same way whatever the grouping.
+ * *ppc_out (may be NULL) receives the choice. */
+int gmg_batch_autotune(gmg_batch* b, int* ppc_out);
+
+/* Set the patches-per-CTA variant explicitly (0, 1, 2 or 4). */
+int gmg_batch_set_ppc(gmg_batch* b, int ppc);
+
 /* Host-only set-up math exposed for testing: the 1D fast-diagonalisation
  * data of one vertex patch built from two cells of unit width (App. A.3):
  * M, K = interior (2k-1)x(2k-1) mass and stiffness of the two-cell 1D

@@ -13,6 +13,7 @@
 
 #include "../../include/gmg.h"
 #include "kernels.h"
+#include "problem.h"
 #include "setup.h"
 
 using namespace gmg;
@@ -21,53 +22,8 @@ static std::atomic<long long> g_launches{0};
 void gmg::count_launch(int n) { g_launches += n; }
 long long gmg::launch_count() { return g_launches.load(); }
 
-namespace {
-
-struct Level {
-  LevelGeom g;
-  long long n_elems = 0;
-  double h = 0.0;
-  void* u = nullptr;  // level correction (problem precision)
-  void* b = nullptr;  // level right-hand side (problem precision)
-  void* r = nullptr;  // level residual (problem precision)
-  // patches of every colour in Z-curve order (Algorithm 5), built on demand
-  int* zlist = nullptr;
-  int zoff[9] = {0};
-};
-
-}  // namespace
-
-struct gmg_problem {
-  gmg_desc desc{};
-  cudaStream_t stream = nullptr;
-  size_t esize = 8;  // bytes per level-vector element
-  std::vector<Level> levels;
-  // patch fast diagonalisation: 1/(sum of eigenvalues) over M^d modes
-  void* dinv = nullptr;
-  // transfer tables (problem precision): prolongation 2k x (k+1),
-  // restriction k x (4k-1)
-  void* coef_prol = nullptr;
-  void* coef_rest = nullptr;
-  void* tmp1 = nullptr;  // transfer temporaries
-  void* tmp2 = nullptr;
-  // coarsest-level fast diagonalisation
-  int m0 = 0;
-  void* coef_c_fwd = nullptr;  // T0^T  (m0 x m0)
-  void* coef_c_bwd = nullptr;  // T0    (m0 x m0)
-  void* dinv0 = nullptr;       // h0^{2-d} / sum lambda
-  void* ctmp1 = nullptr;
-  void* ctmp2 = nullptr;
-  // outer CG (double, finest level)
-  double* cg_r = nullptr;
-  double* cg_z = nullptr;
-  double* cg_p = nullptr;
-  double* cg_q = nullptr;
-  double* partial = nullptr;
-  double* scal = nullptr;  // device scalars, see enum below
-  std::vector<void*> owned;
-};
-
-namespace {
+namespace gmg {
+namespace detail {
 
 enum { S_RZ = 0, S_PQ = 1, S_RR = 2, S_RZN = 3, S_BB = 4, S_COUNT = 8 };
 
@@ -114,11 +70,6 @@ bool valid_level(const gmg_problem* p, int level) {
   return p && level >= 0 && level < (int)p->levels.size();
 }
 
-#define CHECK(x)                 \
-  do {                           \
-    int st_ = (x);               \
-    if (st_ != GMG_OK) return st_; \
-  } while (0)
 
 // ---- typed dispatch helpers ----
 int apply_level(gmg_problem* p, int level, const void* x, void* y, const void* bvec, double alpha,
@@ -408,7 +359,10 @@ int vcycle_level(gmg_problem* p, int l, void* x, const void* b) {
   return GMG_OK;
 }
 
-}  // namespace
+}  // namespace detail
+}  // namespace gmg
+
+using namespace gmg::detail;
 
 extern "C" {
 
@@ -449,7 +403,9 @@ int gmg_destroy(gmg_problem* p) {
   return GMG_OK;
 }
 
-static int create_impl(const gmg_desc* d, gmg_problem* p) {
+}  // extern "C"
+
+int gmg::detail::create_problem(const gmg_desc* d, gmg_problem* p, const CreateOptions& opt) {
   p->desc = *d;
   p->stream = (cudaStream_t)d->stream;
   p->esize = d->precision == GMG_FP32 ? 4 : 8;
@@ -475,6 +431,12 @@ static int create_impl(const gmg_desc* d, gmg_problem* p) {
     lv.g = make_geom(dim, k, n);
     lv.n_elems = geom_elems(lv.g);
     lv.h = 1.0 / n;
+    if (l == L - 1 && opt.finest_u) {
+      lv.u = opt.finest_u;
+      lv.b = opt.finest_b;
+      lv.r = opt.finest_r;
+      continue;
+    }
     CHECK(dalloc(p, &lv.u, lv.n_elems * p->esize));
     CHECK(dalloc(p, &lv.b, lv.n_elems * p->esize));
     CHECK(dalloc(p, &lv.r, lv.n_elems * p->esize));
@@ -555,6 +517,7 @@ static int create_impl(const gmg_desc* d, gmg_problem* p) {
   CHECK(dalloc(p, &p->ctmp1, nm0 * p->esize));
   CHECK(dalloc(p, &p->ctmp2, nm0 * p->esize));
   // outer CG
+  if (opt.no_cg) return cudaDeviceSynchronize() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
   const long long nf = p->levels[L - 1].n_elems;
   CHECK(dalloc(p, (void**)&p->cg_r, nf * 8));
   CHECK(dalloc(p, (void**)&p->cg_z, nf * 8));
@@ -565,9 +528,7 @@ static int create_impl(const gmg_desc* d, gmg_problem* p) {
   return cudaDeviceSynchronize() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
 }
 
-int gmg_create(const gmg_desc* d, gmg_problem** out) {
-  if (!out) return GMG_ERR_INVALID_ARG;
-  *out = nullptr;
+int gmg::detail::check_desc(const gmg_desc* d) {
   if (!d) return GMG_ERR_INVALID_ARG;
   if (d->dim != 2 && d->dim != 3) return GMG_ERR_INVALID_ARG;
   if (d->degree < 1 || d->degree > kMaxDegree) return GMG_ERR_INVALID_ARG;
@@ -576,9 +537,18 @@ int gmg_create(const gmg_desc* d, gmg_problem** out) {
   if (!std::isfinite(d->damping) || d->pre_sweeps < 0 || d->post_sweeps < 0) return GMG_ERR_INVALID_ARG;
   // node counts must fit 32-bit lattice indices
   if ((long long)d->n_cells * d->degree + 1 > (1 << 20)) return GMG_ERR_INVALID_ARG;
+  return GMG_OK;
+}
+
+extern "C" {
+
+int gmg_create(const gmg_desc* d, gmg_problem** out) {
+  if (!out) return GMG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (check_desc(d) != GMG_OK) return GMG_ERR_INVALID_ARG;
   gmg_problem* p = new (std::nothrow) gmg_problem();
   if (!p) return GMG_ERR_OOM;
-  int st = create_impl(d, p);
+  int st = create_problem(d, p, CreateOptions());
   if (st != GMG_OK) {
     gmg_destroy(p);
     return st;

@@ -34,6 +34,29 @@ struct PatchLaunch {
   int mode;
 };
 
+// One launch of the sweep kernel covers one colour of up to kMaxTable
+// problems (or level slices): entry i owns groups [group_begin, group_begin
+// + ceil(n_patches / PPC)) of the launch.  Passed by value as a kernel
+// parameter.
+constexpr int kMaxTable = 64;
+struct PatchEntry {
+  long long py, pz;     // pitches of the level vectors
+  int first[3], count[3];
+  int n_patches;
+  int group_begin;
+  double sb;            // h^{2-d}
+  void* u;              // level vector updated in place
+  const void* b;        // right-hand side (or residual in solve-only mode)
+  const int* plist;     // optional patch list (lexicographic ids in the colour)
+};
+struct PatchTable {
+  int n;                // entries used
+  int total_groups;
+  int mode;             // 0 combined (Algorithm 4), 1 solve only (Algorithm 3)
+  double omega;
+  PatchEntry e[kMaxTable];
+};
+
 // y = alpha * (A_ref x) + beta * bvec on owned interior nodes, where A_ref is
 // the level operator assembled from unit cells (A = h^{d-2} A_ref).
 struct ApplyLaunch {
@@ -70,6 +93,12 @@ int upload_patch_tables(int k, const double* Mp, const double* Kp, const double*
                         const double* Mc, const double* Kc, cudaStream_t s);
 template <typename T>
 int launch_patch_colour(const PatchLaunch& pl, T* u, const T* b, const T* dinv, cudaStream_t s);
+// several problems / slices of one colour in one launch (all of dimension
+// dim and degree k); ppc = 0 picks the default patches per CTA, else one of
+// the tuned variants 1, 2, 4 (3D FP32 only; others use the default)
+template <typename T>
+int launch_patch_table(int dim, int k, const PatchLaunch* pls, T* const* us, const T* const* bs,
+                       int n, const T* dinv, int ppc, cudaStream_t s);
 template <typename T>
 int launch_apply(const ApplyLaunch& al, const T* x, T* y, const T* bvec, cudaStream_t s);
 
@@ -94,5 +123,29 @@ int launch_cg_update(long long n, double* x, double* r, const double* p, const d
 // p = z + (num/den) p
 int launch_cg_direction(long long n, double* p, const double* z, const double* num,
                         const double* den, cudaStream_t s);
+
+// Segmented (per-problem) FP64 vector kernels over concatenated vectors.  The
+// concatenation is cut into chunks; chunk c covers elements [start[c],
+// start[c] + len[c]) and belongs to problem owner[c]; problem i owns chunks
+// [begin[i], begin[i+1]).  Per-problem scalars are arrays indexed by problem.
+struct Segments {
+  int n_chunks = 0;
+  int n_problems = 0;
+  const long long* start = nullptr;  // device arrays
+  const int* len = nullptr;
+  const int* owner = nullptr;
+  const int* begin = nullptr;        // n_problems + 1
+};
+constexpr int kSegChunk = 8192;
+// result[i] = x_i . y_i
+int launch_seg_dot(const Segments& sg, const double* x, const double* y, double* partial,
+                   double* result, cudaStream_t s);
+// for active problems: x += (num/den) p, r -= (num/den) q; result[i] = r_i . r_i
+int launch_seg_cg_update(const Segments& sg, double* x, double* r, const double* p, const double* q,
+                         const double* num, const double* den, const int* active, double* partial,
+                         double* result, cudaStream_t s);
+// for active problems: p = z + (num/den) p
+int launch_seg_cg_direction(const Segments& sg, double* p, const double* z, const double* num,
+                            const double* den, const int* active, cudaStream_t s);
 
 }  // namespace gmg

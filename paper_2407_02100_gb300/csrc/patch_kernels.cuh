@@ -172,8 +172,8 @@ struct SweepSmem {
 // Same-colour patches never write each other's closure, so the buffered
 // closure values are the values the gather (eq. "gather") reads.
 template <int DIM, int K, int NT, int PPC, int NBUF>
-__global__ void __launch_bounds__(NT) patch_colour_kernel(T* __restrict__ u, const T* __restrict__ b,
-                                                          const T* __restrict__ dinv, PatchLaunch pl) {
+__global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant__ PatchTable tab,
+                                                          const T* __restrict__ dinv) {
   using Z = SweepSmem<DIM, K>;
   constexpr int C = Z::C, M = Z::M;
   constexpr int LINES = DIM == 3 ? M * M : M;  // interior lines per axis
@@ -183,35 +183,51 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(T* __restrict__ u, con
   T* const WB = WA + PPC * Z::WA;                      // [PPC][WB]
   __shared__ long long s_origin[2][PPC];
   __shared__ int s_nvalid[2];
-  const long long py = pl.g.py, pz = pl.g.pz;
-  const T sb = (T)pl.sb;
-  const T om = (T)pl.omega;
-  const int ngroups = (pl.n_patches + PPC - 1) / PPC;
+  __shared__ int s_entry[2];
+  const T om = (T)tab.omega;
+  const int mode = tab.mode;
+  const int ngroups = tab.total_groups;
 
-  // patch origins of a group (threads 0..PPC-1); callers follow with a barrier
+  // table entry and patch origins of a group (threads 0..PPC-1); callers
+  // follow with a barrier
   auto set_origins = [&](int grp, int slot) {
-    const int nv = min(PPC, pl.n_patches - grp * PPC);
-    if (threadIdx.x == 0) s_nvalid[slot] = nv;
+    int lo = 0, hi = tab.n - 1;  // last entry with group_begin <= grp
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tab.e[mid].group_begin <= grp) lo = mid;
+      else hi = mid - 1;
+    }
+    const PatchEntry& e = tab.e[lo];
+    const int g = grp - e.group_begin;
+    const int nv = min(PPC, e.n_patches - g * PPC);
+    if (threadIdx.x == 0) {
+      s_nvalid[slot] = nv;
+      s_entry[slot] = lo;
+    }
     if (threadIdx.x < nv) {
-      int pid = grp * PPC + threadIdx.x;
-      if (pl.plist) pid = pl.plist[pid];
-      const int i0 = pid % pl.count[0];
-      const int rest = pid / pl.count[0];
-      const int i1 = rest % pl.count[1];
-      const int i2 = DIM == 3 ? rest / pl.count[1] : 0;
-      const long long o0 = (long long)(pl.first[0] + 2 * i0 - 1) * K;
-      const long long o1 = (long long)(pl.first[1] + 2 * i1 - 1) * K;
-      const long long o2 = DIM == 3 ? (long long)(pl.first[2] + 2 * i2 - 1) * K : 0;
-      s_origin[slot][threadIdx.x] = o0 + py * o1 + pz * o2;
+      int pid = g * PPC + threadIdx.x;
+      if (e.plist) pid = e.plist[pid];
+      const int i0 = pid % e.count[0];
+      const int rest = pid / e.count[0];
+      const int i1 = rest % e.count[1];
+      const int i2 = DIM == 3 ? rest / e.count[1] : 0;
+      const long long o0 = (long long)(e.first[0] + 2 * i0 - 1) * K;
+      const long long o1 = (long long)(e.first[1] + 2 * i1 - 1) * K;
+      const long long o2 = DIM == 3 ? (long long)(e.first[2] + 2 * i2 - 1) * K : 0;
+      s_origin[slot][threadIdx.x] = o0 + e.py * o1 + e.pz * o2;
     }
   };
   // issue the copies of the group whose origins are in `slot` into input
   // buffer `slot`, then commit them as one group
   auto prefetch = [&](int slot) {
     const int nv = s_nvalid[slot];
+    const PatchEntry& e = tab.e[s_entry[slot]];
+    const T* __restrict__ u = static_cast<const T*>(e.u);
+    const T* __restrict__ b = static_cast<const T*>(e.b);
+    const long long py = e.py, pz = e.pz;
     T* dst0 = IN0 + slot * PPC * Z::IN;
     // the solve-only mode needs no closure: only the residual's interior
-    for (int idx = threadIdx.x; idx < (pl.mode == 0 ? nv * Z::NCLO : 0); idx += NT) {  // closure of u
+    for (int idx = threadIdx.x; idx < (mode == 0 ? nv * Z::NCLO : 0); idx += NT) {  // closure of u
       const int q = idx / Z::NCLO, t = idx % Z::NCLO;
       const int x = t % C, row = t / C;
       const long long g = s_origin[slot][q] + x + py * (row % C) + (DIM == 3 ? pz * (row / C) : 0);
@@ -251,8 +267,12 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(T* __restrict__ u, con
     __syncthreads();  // ... and everybody's
     const int nvalid = s_nvalid[cur];
     const T* IN = IN0 + cur * PPC * Z::IN;
+    const PatchEntry& ec = tab.e[s_entry[cur]];
+    T* __restrict__ u = static_cast<T*>(ec.u);
+    const long long py = ec.py, pz = ec.pz;
+    const T sb = (T)ec.sb;
 
-    if (pl.mode != 0) {
+    if (mode != 0) {
       // solve only: nothing to evaluate, the buffer holds the residual
     } else if (DIM == 3) {
       // ---- stage z: P = Mp_z u, Q = Kp_z u   (dims x:C, y:C, z:M, in WB) ----
@@ -316,7 +336,7 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(T* __restrict__ u, con
       const T* X = WA + q * Z::WA;
       const T* Bq = IN + q * Z::IN + Z::NCLO;
       T r[M], y[M];
-      if (pl.mode == 0) {
+      if (mode == 0) {
         T a1[C], a2[C];
 #pragma unroll
         for (int j = 0; j < C; ++j) {
@@ -389,7 +409,7 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(T* __restrict__ u, con
       const long long row = s_origin[cur][q] + 1 + py * (l % M + 1) + (DIM == 3 ? pz * (l / M + 1) : 0);
 #pragma unroll
       for (int i = 0; i < M; ++i)
-        u[row + i] = fma(om, d[i], pl.mode == 0 ? U[cl + 1 + i] : u[row + i]);
+        u[row + i] = fma(om, d[i], mode == 0 ? U[cl + 1 + i] : u[row + i]);
     }
     __syncthreads();  // buffers and origins are refilled / reused next iteration
   }

@@ -56,23 +56,93 @@ static int prepare(KernelT kern, int smem) {
   return GMG_OK;
 }
 
-template <int DIM, int K>
-static int patch_impl(const PatchLaunch& pl, T* u, const T* b, const T* dinv, cudaStream_t s) {
-  using Cfg = SweepCfg<DIM, K>;
-  auto kern = patch_colour_kernel<DIM, K, Cfg::NT, Cfg::PPC, Cfg::NBUF>;
+// Fill the table entries' group ranges for PPC patches per CTA.
+static inline int table_groups(PatchTable& tab, int ppc) {
+  int g = 0;
+  for (int i = 0; i < tab.n; ++i) {
+    tab.e[i].group_begin = g;
+    g += (tab.e[i].n_patches + ppc - 1) / ppc;
+  }
+  tab.total_groups = g;
+  return g;
+}
+
+template <int DIM, int K, int PPC, int NT, int NBUF>
+static int launch_table_cfg(PatchTable& tab, const T* dinv, cudaStream_t s) {
+  constexpr int SMEM = PPC * SweepSmem<DIM, K>::per_patch(NBUF) * (int)sizeof(T);
+  static_assert(SMEM <= 227 * 1024, "sweep kernel shared memory exceeds the per-CTA limit");
+  auto kern = patch_colour_kernel<DIM, K, NT, PPC, NBUF>;
   static int per_sm = 0;  // resident CTAs per SM (persistent grid)
   if (per_sm == 0) {
-    if (prepare(kern, Cfg::SMEM) != GMG_OK) return GMG_ERR_CUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::NT, Cfg::SMEM) != cudaSuccess ||
+    if (prepare(kern, SMEM) != GMG_OK) return GMG_ERR_CUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, SMEM) != cudaSuccess ||
         per_sm <= 0)
       return GMG_ERR_CUDA;
   }
-  if (pl.n_patches <= 0) return GMG_OK;
-  const int ngroups = (pl.n_patches + Cfg::PPC - 1) / Cfg::PPC;
+  const int ngroups = table_groups(tab, PPC);
+  if (ngroups <= 0) return GMG_OK;
   const int grid = std::min(ngroups, per_sm * sm_count());
-  kern<<<grid, Cfg::NT, Cfg::SMEM, s>>>(u, b, dinv, pl);
+  kern<<<grid, NT, SMEM, s>>>(tab, dinv);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+}
+
+// default configuration (SweepCfg), or a tuned patches-per-CTA variant
+template <int DIM, int K>
+static int launch_table(PatchTable& tab, const T* dinv, int ppc, cudaStream_t s) {
+  using Cfg = SweepCfg<DIM, K>;
+  if constexpr (DIM == 3 && sizeof(T) == 4 && K <= 4) {
+    constexpr int NB = SweepCfg<DIM, K>::NBUF;
+    if (ppc == 1) return launch_table_cfg<DIM, K, 1, 128, NB>(tab, dinv, s);
+    if (ppc == 2) return launch_table_cfg<DIM, K, 2, 128, NB>(tab, dinv, s);
+    if (ppc == 4) return launch_table_cfg<DIM, K, 4, 128, NB>(tab, dinv, s);
+  }
+  return launch_table_cfg<DIM, K, Cfg::PPC, Cfg::NT, Cfg::NBUF>(tab, dinv, s);
+}
+
+static void fill_entry(PatchEntry& e, const PatchLaunch& pl, void* u, const void* b) {
+  e.py = pl.g.py;
+  e.pz = pl.g.pz;
+  for (int a = 0; a < 3; ++a) {
+    e.first[a] = pl.first[a];
+    e.count[a] = pl.count[a];
+  }
+  e.n_patches = pl.n_patches;
+  e.group_begin = 0;
+  e.sb = pl.sb;
+  e.u = u;
+  e.b = b;
+  e.plist = pl.plist;
+}
+
+template <int DIM, int K>
+static int patch_impl(const PatchLaunch& pl, T* u, const T* b, const T* dinv, cudaStream_t s) {
+  if (pl.n_patches <= 0) return GMG_OK;
+  PatchTable tab;
+  tab.n = 1;
+  tab.mode = pl.mode;
+  tab.omega = pl.omega;
+  fill_entry(tab.e[0], pl, u, b);
+  return launch_table<DIM, K>(tab, dinv, 0, s);
+}
+
+template <int DIM, int K>
+static int table_impl(const PatchLaunch* pls, T* const* us, const T* const* bs, int n, const T* dinv,
+                      int ppc, cudaStream_t s) {
+  for (int i0 = 0; i0 < n; i0 += kMaxTable) {
+    PatchTable tab;
+    tab.n = 0;
+    tab.mode = pls[i0].mode;
+    tab.omega = pls[i0].omega;
+    for (int i = i0; i < std::min(n, i0 + kMaxTable); ++i) {
+      if (pls[i].n_patches <= 0) continue;
+      fill_entry(tab.e[tab.n++], pls[i], us[i], bs[i]);
+    }
+    if (tab.n == 0) continue;
+    const int st = launch_table<DIM, K>(tab, dinv, ppc, s);
+    if (st != GMG_OK) return st;
+  }
+  return GMG_OK;
 }
 
 template <int DIM, int K>
@@ -80,7 +150,11 @@ static int apply_impl(const ApplyLaunch& al, const T* x, T* y, const T* bvec, cu
   constexpr int BC = apply_bc(DIM, K);
   using D = ApplyDims<DIM, K, BC>;
   auto kern = apply_kernel<DIM, K, BC, kApplyThreads>;
-  if (prepare(kern, D::SMEM_BYTES) != GMG_OK) return GMG_ERR_CUDA;
+  static bool ready = false;  // attribute set once (also keeps graph capture free of it)
+  if (!ready) {
+    if (prepare(kern, D::SMEM_BYTES) != GMG_OK) return GMG_ERR_CUDA;
+    ready = true;
+  }
   long long tiles = (al.g.n + BC - 1) / BC;
   long long ntile = DIM == 3 ? tiles * tiles * tiles : tiles * tiles;
   int grid = (int)std::min<long long>(ntile, 1 << 30);
@@ -139,6 +213,13 @@ template <>
 int launch_patch_colour<GMG_T>(const PatchLaunch& pl, GMG_T* u, const GMG_T* b, const GMG_T* dinv,
                                cudaStream_t s) {
   GMG_DISPATCH(GMG_NS::patch_impl, pl.g.dim, pl.g.k, pl, u, b, dinv, s)
+}
+
+template <>
+int launch_patch_table<GMG_T>(int dim, int k, const PatchLaunch* pls, GMG_T* const* us,
+                              const GMG_T* const* bs, int n, const GMG_T* dinv, int ppc,
+                              cudaStream_t s) {
+  GMG_DISPATCH(GMG_NS::table_impl, dim, k, pls, us, bs, n, dinv, ppc, s)
 }
 
 template <>

@@ -1,0 +1,95 @@
+// Internal definitions shared by the C ABI translation units (api.cu,
+// batch.cu): the problem object and the level operations the V-cycles are
+// built from.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/gmg.h"
+#include "kernels.h"
+
+namespace gmg {
+namespace detail {
+
+struct Level {
+  LevelGeom g;
+  long long n_elems = 0;
+  double h = 0.0;
+  void* u = nullptr;  // level correction (problem precision)
+  void* b = nullptr;  // level right-hand side (problem precision)
+  void* r = nullptr;  // level residual (problem precision)
+  // patches of every colour in Z-curve order (Algorithm 5), built on demand
+  int* zlist = nullptr;
+  int zoff[9] = {0};
+};
+
+// Options of problem creation used by batches: the finest level's u, b, r
+// may live in caller-owned slices, and the outer-CG vectors may be omitted.
+struct CreateOptions {
+  void* finest_u = nullptr;
+  void* finest_b = nullptr;
+  void* finest_r = nullptr;
+  bool no_cg = false;
+};
+
+}  // namespace detail
+}  // namespace gmg
+
+struct gmg_problem {
+  gmg_desc desc{};
+  cudaStream_t stream = nullptr;
+  size_t esize = 8;  // bytes per level-vector element
+  std::vector<gmg::detail::Level> levels;
+  // patch fast diagonalisation: 1/(sum of eigenvalues) over M^d modes
+  void* dinv = nullptr;
+  // transfer tables (problem precision): prolongation 2k x (k+1),
+  // restriction k x (4k-1)
+  void* coef_prol = nullptr;
+  void* coef_rest = nullptr;
+  void* tmp1 = nullptr;  // transfer temporaries
+  void* tmp2 = nullptr;
+  // coarsest-level fast diagonalisation
+  int m0 = 0;
+  void* coef_c_fwd = nullptr;  // T0^T  (m0 x m0)
+  void* coef_c_bwd = nullptr;  // T0    (m0 x m0)
+  void* dinv0 = nullptr;       // h0^{2-d} / sum lambda
+  void* ctmp1 = nullptr;
+  void* ctmp2 = nullptr;
+  // outer CG (double, finest level)
+  double* cg_r = nullptr;
+  double* cg_z = nullptr;
+  double* cg_p = nullptr;
+  double* cg_q = nullptr;
+  double* partial = nullptr;
+  double* scal = nullptr;  // device scalars
+  std::vector<void*> owned;
+};
+
+namespace gmg {
+namespace detail {
+
+#define CHECK(x)                   \
+  do {                             \
+    int st_ = (x);                 \
+    if (st_ != GMG_OK) return st_; \
+  } while (0)
+
+int dalloc(gmg_problem* p, void** ptr, size_t bytes);
+LevelGeom make_geom(int dim, int k, int n);
+long long geom_elems(const LevelGeom& g);
+double op_scale(const Level& L);  // h^{d-2}
+int apply_level(gmg_problem* p, int level, const void* x, void* y, const void* bvec, double alpha,
+                double beta);
+PatchLaunch colour_launch(const Level& L, int colour, double omega);
+int launch_colour(gmg_problem* p, const PatchLaunch& pl, void* u, const void* b);
+int smooth(gmg_problem* p, int level, void* u, const void* b, int n_sweeps, int reverse);
+int prolongate_add(gmg_problem* p, int cl, const void* coarse, void* fine);
+int restrict_to(gmg_problem* p, int fl, const void* fine, void* coarse);
+int coarse_solve(gmg_problem* p, const void* b, void* x);
+int vcycle_level(gmg_problem* p, int l, void* x, const void* b);
+int create_problem(const gmg_desc* d, gmg_problem* p, const CreateOptions& opt);
+int check_desc(const gmg_desc* d);
+
+}  // namespace detail
+}  // namespace gmg

@@ -129,6 +129,63 @@ __global__ void cg_direction_kernel(long long n, double* __restrict__ p, const d
     p[i] = z[i] + beta * p[i];
 }
 
+constexpr int kSegThreads = 256;
+
+__global__ void seg_dot_kernel(Segments sg, const double* __restrict__ x, const double* __restrict__ y,
+                               double* __restrict__ partial) {
+  const int c = blockIdx.x;
+  const long long s0 = sg.start[c];
+  const int n = sg.len[c];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += kSegThreads) acc += x[s0 + i] * y[s0 + i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[c] = acc;
+}
+
+__global__ void seg_final_kernel(Segments sg, const double* __restrict__ partial, double* __restrict__ result) {
+  const int i = blockIdx.x;
+  double acc = 0.0;
+  for (int c = sg.begin[i] + threadIdx.x; c < sg.begin[i + 1]; c += kSegThreads) acc += partial[c];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) result[i] = acc;
+}
+
+__global__ void seg_update_kernel(Segments sg, double* __restrict__ x, double* __restrict__ r,
+                                  const double* __restrict__ p, const double* __restrict__ q,
+                                  const double* __restrict__ num, const double* __restrict__ den,
+                                  const int* __restrict__ active, double* __restrict__ partial) {
+  const int c = blockIdx.x;
+  const int owner = sg.owner[c];
+  const long long s0 = sg.start[c];
+  const int n = sg.len[c];
+  const bool on = active[owner] != 0;
+  const double alpha = on ? num[owner] / den[owner] : 0.0;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += kSegThreads) {
+    double ri = r[s0 + i];
+    if (on) {
+      x[s0 + i] += alpha * p[s0 + i];
+      ri -= alpha * q[s0 + i];
+      r[s0 + i] = ri;
+    }
+    acc += ri * ri;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[c] = acc;
+}
+
+__global__ void seg_direction_kernel(Segments sg, double* __restrict__ p, const double* __restrict__ z,
+                                     const double* __restrict__ num, const double* __restrict__ den,
+                                     const int* __restrict__ active) {
+  const int c = blockIdx.x;
+  const int owner = sg.owner[c];
+  if (!active[owner]) return;
+  const long long s0 = sg.start[c];
+  const int n = sg.len[c];
+  const double beta = num[owner] / den[owner];
+  for (int i = threadIdx.x; i < n; i += kSegThreads) p[s0 + i] = z[s0 + i] + beta * p[s0 + i];
+}
+
 inline int status(int launches = 1) {
   count_launch(launches);
   return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
@@ -179,6 +236,30 @@ int launch_cg_update(long long n, double* x, double* r, const double* p, const d
   cg_update_kernel<<<g, kThreads, 0, s>>>(n, x, r, p, q, num, den, partial);
   final_sum_kernel<<<1, kThreads, 0, s>>>(g, partial, result);
   return status(2);
+}
+
+int launch_seg_dot(const Segments& sg, const double* x, const double* y, double* partial,
+                   double* result, cudaStream_t s) {
+  if (sg.n_chunks <= 0) return GMG_OK;
+  seg_dot_kernel<<<sg.n_chunks, kSegThreads, 0, s>>>(sg, x, y, partial);
+  seg_final_kernel<<<sg.n_problems, kSegThreads, 0, s>>>(sg, partial, result);
+  return status(2);
+}
+
+int launch_seg_cg_update(const Segments& sg, double* x, double* r, const double* p, const double* q,
+                         const double* num, const double* den, const int* active, double* partial,
+                         double* result, cudaStream_t s) {
+  if (sg.n_chunks <= 0) return GMG_OK;
+  seg_update_kernel<<<sg.n_chunks, kSegThreads, 0, s>>>(sg, x, r, p, q, num, den, active, partial);
+  seg_final_kernel<<<sg.n_problems, kSegThreads, 0, s>>>(sg, partial, result);
+  return status(2);
+}
+
+int launch_seg_cg_direction(const Segments& sg, double* p, const double* z, const double* num,
+                            const double* den, const int* active, cudaStream_t s) {
+  if (sg.n_chunks <= 0) return GMG_OK;
+  seg_direction_kernel<<<sg.n_chunks, kSegThreads, 0, s>>>(sg, p, z, num, den, active);
+  return status();
 }
 
 int launch_cg_direction(long long n, double* p, const double* z, const double* num,

@@ -27,7 +27,9 @@ EXPORTS = ["gmg_create", "gmg_destroy", "gmg_vector_layout", "gmg_level_info",
            "gmg_apply_operator", "gmg_apply_operator_f64", "gmg_smooth", "gmg_smooth_colour",
            "gmg_restrict", "gmg_prolongate_add", "gmg_coarse_solve", "gmg_vcycle",
            "cg_gmg_solve", "gmg_patch_fd_1d", "gmg_kernel_launch_count", "gmg_status_string",
-           "gmg_smooth_noalloc", "gmg_smooth_variant"]
+           "gmg_smooth_noalloc", "gmg_smooth_variant", "gmg_batch_create", "gmg_batch_destroy",
+           "gmg_batch_layout", "gmg_batch_problem", "gmg_batch_smooth", "gmg_batch_vcycle",
+           "gmg_batch_cg_solve", "gmg_batch_autotune", "gmg_batch_set_ppc"]
 GMG_SWEEP_COMBINED, GMG_SWEEP_SEPARATED, GMG_SWEEP_BATCHED = 0, 1, 2
 
 
@@ -79,6 +81,15 @@ def lib():
             "cg_gmg_solve": [vp, vp, vp, d, i, ctypes.POINTER(GmgSolveStats)],
             "gmg_patch_fd_1d": [i, vp, vp, vp, vp],
             "gmg_kernel_launch_count": [],
+            "gmg_batch_create": [ctypes.POINTER(GmgDesc), i, ctypes.POINTER(i), ctypes.POINTER(vp)],
+            "gmg_batch_destroy": [vp],
+            "gmg_batch_layout": [vp, i, ctypes.POINTER(ll), ctypes.POINTER(ll), ctypes.POINTER(ll)],
+            "gmg_batch_problem": [vp, i, ctypes.POINTER(vp)],
+            "gmg_batch_smooth": [vp, vp, vp, i],
+            "gmg_batch_vcycle": [vp, vp, vp],
+            "gmg_batch_cg_solve": [vp, vp, vp, d, i, ctypes.POINTER(i), ctypes.POINTER(d)],
+            "gmg_batch_autotune": [vp, ctypes.POINTER(i)],
+            "gmg_batch_set_ppc": [vp, i],
             "gmg_smooth_noalloc": [i, i, i, d, vp, vp, i, i, vp],
             "gmg_status_string": [i],
         }
@@ -268,3 +279,119 @@ class Problem:
         if self.dim == 2:
             return v.view(N, py)[:, :N].reshape(-1).numpy().copy()
         return v.view(N, N, py)[:, :, :N].reshape(-1).numpy().copy()
+
+
+# ---------------------------------------------------------------------------
+# batches of independent problems
+
+def gmg_batch_create(dim, degree, n_cells, precision=GMG_FP64, damping=1.0, pre_sweeps=1,
+                     post_sweeps=1, stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    desc = GmgDesc(dim, degree, 0, 0, precision, damping, pre_sweeps, post_sweeps, ctypes.c_void_p(stream))
+    arr = (ctypes.c_int * len(n_cells))(*[int(n) for n in n_cells])
+    h = ctypes.c_void_p()
+    _check("gmg_batch_create", lib().gmg_batch_create(ctypes.byref(desc), len(n_cells), arr, ctypes.byref(h)))
+    return h
+
+
+def gmg_batch_destroy(h):
+    _check("gmg_batch_destroy", lib().gmg_batch_destroy(h))
+
+
+def gmg_batch_layout(h, problem):
+    o, n, t = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    _check("gmg_batch_layout", lib().gmg_batch_layout(h, problem, ctypes.byref(o), ctypes.byref(n), ctypes.byref(t)))
+    return o.value, n.value, t.value
+
+
+def gmg_batch_problem(h, problem):
+    out = ctypes.c_void_p()
+    _check("gmg_batch_problem", lib().gmg_batch_problem(h, problem, ctypes.byref(out)))
+    return out
+
+
+def gmg_batch_smooth(h, u, b, reverse=False):
+    _check("gmg_batch_smooth", lib().gmg_batch_smooth(h, _ptr(u), _ptr(b), int(bool(reverse))))
+
+
+def gmg_batch_vcycle(h, x, b):
+    _check("gmg_batch_vcycle", lib().gmg_batch_vcycle(h, _ptr(x), _ptr(b)))
+
+
+def gmg_batch_cg_solve(h, n_problems, u, b, rtol=1e-10, max_it=100, raise_on_error=True):
+    its = (ctypes.c_int * n_problems)()
+    res = (ctypes.c_double * n_problems)()
+    st = lib().gmg_batch_cg_solve(h, _ptr(u), _ptr(b), rtol, max_it, its, res)
+    if raise_on_error:
+        _check("gmg_batch_cg_solve", st)
+    return st, list(its), list(res)
+
+
+def gmg_batch_autotune(h):
+    out = ctypes.c_int()
+    _check("gmg_batch_autotune", lib().gmg_batch_autotune(h, ctypes.byref(out)))
+    return out.value
+
+
+def gmg_batch_set_ppc(h, ppc):
+    _check("gmg_batch_set_ppc", lib().gmg_batch_set_ppc(h, ppc))
+
+
+class Batch:
+    """Owns one gmg_batch; batch vectors are single CUDA tensors holding the
+    padded finest-level vectors of all problems at their offsets."""
+
+    def __init__(self, dim, degree, n_cells, precision=GMG_FP64, damping=1.0, stream=None):
+        import torch
+        self.torch = torch
+        self.dim, self.degree, self.n_cells = dim, degree, list(n_cells)
+        self.dtype = torch.float64 if precision == GMG_FP64 else torch.float32
+        self.h = gmg_batch_create(dim, degree, self.n_cells, precision, damping, stream=stream)
+        self.layouts = []
+        for i in range(len(self.n_cells)):
+            off, n, total = gmg_batch_layout(self.h, i)
+            p = gmg_batch_problem(self.h, i)
+            nl = gmg_level_info(p, 0)[1]
+            self.layouts.append((off, n, gmg_vector_layout(p, nl - 1)))
+        self.total = total
+
+    def close(self):
+        if self.h is not None:
+            gmg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def zeros(self, dtype=None):
+        return self.torch.zeros(self.total, dtype=dtype or self.dtype, device="cuda")
+
+    def pack(self, dense_list, dtype=None):
+        """Dense per-problem node arrays -> one padded batch vector (device)."""
+        t = self.torch
+        out = t.zeros(self.total, dtype=dtype or self.dtype)
+        for (off, n, (ne, N, py, pz)), dense in zip(self.layouts, dense_list):
+            v = out[off:off + n]
+            d = t.as_tensor(np.asarray(dense)).to(out.dtype)
+            if self.dim == 2:
+                v.view(N, py)[:, :N] = d.view(N, N)
+            else:
+                v.view(N, N, py)[:, :, :N] = d.view(N, N, N)
+        return out.cuda()
+
+    def unpack(self, vec):
+        """Batch vector -> list of dense float64 numpy node arrays."""
+        v = vec.detach().to("cpu", self.torch.float64)
+        out = []
+        for off, n, (ne, N, py, pz) in self.layouts:
+            w = v[off:off + n]
+            if self.dim == 2:
+                out.append(w.view(N, py)[:, :N].reshape(-1).numpy().copy())
+            else:
+                out.append(w.view(N, N, py)[:, :, :N].reshape(-1).numpy().copy())
+        return out
