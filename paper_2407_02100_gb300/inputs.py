@@ -49,3 +49,32 @@ def sample_vertices(dim, n_cells, count, seed):
         tries += 1
         out.add(tuple(int(x) for x in rng.integers(1, n_cells, size=dim)))
     return np.array(sorted(out, key=lambda t: t[::-1]), dtype=np.int64).reshape(-1, dim)
+
+
+def gaussian_random_field(dim, n_cells, seed, sigma=1.0, corr_len=0.1):
+    """Per-cell values of a stationary Gaussian random field with squared-
+    exponential covariance sigma^2 exp(-r^2 / (2 corr_len^2)), sampled at the
+    cell centres of a uniform n^dim mesh of the unit cube by circulant
+    embedding on a periodic grid of 2n points per direction (spacing 1/n),
+    from numpy.random.default_rng(seed).  Returns shape (n,)*dim indexed
+    [c_{dim-1}, ..., c_0] (C-order flattening = c_0 fastest)."""
+    m = 2 * n_cells
+    h = 1.0 / n_cells
+    d1 = np.minimum(np.arange(m), m - np.arange(m)) * h          # periodic distances
+    r2 = np.zeros((m,) * dim)
+    for a in range(dim):
+        shape = [1] * dim
+        shape[a] = m
+        r2 = r2 + (d1 ** 2).reshape(shape)
+    cov = sigma ** 2 * np.exp(-r2 / (2.0 * corr_len ** 2))
+    lam = np.real(np.fft.fftn(cov))
+    lam = np.maximum(lam, 0.0)                                    # clip round-off negatives
+    rng = np.random.default_rng(seed)
+    xi = rng.standard_normal((m,) * dim)
+    g = np.real(np.fft.ifftn(np.sqrt(lam) * np.fft.fftn(xi)))
+    return g[(slice(0, n_cells),) * dim].copy()
+
+
+def lognormal_coefficient(dim, n_cells, seed, sigma=1.0, corr_len=0.1):
+    """a = exp(g) per cell, g from gaussian_random_field (float64)."""
+    return np.exp(gaussian_random_field(dim, n_cells, seed, sigma, corr_len))
