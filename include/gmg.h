@@ -57,6 +57,11 @@ enum gmg_sweep_variant {
   GMG_SWEEP_BATCHED = 2     /* Algorithm 5: Z-curve batches of n_B patches per colour */
 };
 
+enum gmg_local_solver {
+  GMG_LOCAL_FD_MEAN = 0,   /* FD of the constant-coefficient patch, scaled by the mean coefficient */
+  GMG_LOCAL_LEARNED = 1    /* the same plus the learned rank-R correction (gmg_learned_train) */
+};
+
 typedef struct gmg_problem gmg_problem; /* opaque; owns all level data */
 
 typedef struct {
@@ -245,6 +250,25 @@ int gmg_batch_autotune(gmg_batch* b, int* ppc_out);
 
 /* Set the patches-per-CTA variant explicitly (0, 1, 2 or 4). */
 int gmg_batch_set_ppc(gmg_batch* b, int ppc);
+
+/* ---- Variable coefficient ------------------------------------------------
+ * Switch the problem to -div(a grad u) with one coefficient per cell of the
+ * finest mesh: coef is a HOST array of n_cells^dim positive values, cell
+ * (c_0, c_1[, c_2]) at c_0 + n c_1 [+ n^2 c_2].  Coarser levels take the
+ * geometric mean of their 2^dim children; the coarse solve becomes the dense
+ * inverse of the coarsest interior matrix (at most 2000 unknowns).  The patch
+ * local residual is evaluated cell by cell with the coefficients (the paper's
+ * local_update, Sec. 3.1); since fast diagonalisation is then only
+ * approximate (App. A.3 assumes a tensor-product patch matrix), the local
+ * solver is the constant-coefficient FD scaled by the geometric mean of the
+ * patch's cell coefficients (GMG_LOCAL_FD_MEAN), optionally corrected by
+ * the learned low-rank term (GMG_LOCAL_LEARNED).  Degrees 1..3 only
+ * (GMG_ERR_UNSUPPORTED otherwise); only the combined sweep variant. */
+int gmg_set_coefficient(gmg_problem* p, const double* coef);
+
+/* Select the local solver of a variable-coefficient problem; LEARNED needs a
+ * completed gmg_learned_train. */
+int gmg_set_local_solver(gmg_problem* p, int solver);
 
 /* Host-only set-up math exposed for testing: the 1D fast-diagonalisation
  * data of one vertex patch built from two cells of unit width (App. A.3):

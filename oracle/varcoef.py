@@ -102,7 +102,8 @@ class VarPatchSmoother:
 class VarMultigrid:
     """V(1,1)-cycle and PCG for -div(a grad u), assembled operators."""
 
-    def __init__(self, dim, degree, n_cells, n_levels, coef, mode="exact", corrections=None):
+    def __init__(self, dim, degree, n_cells, n_levels, coef, mode="exact", corrections=None,
+                 omega=1.0):
         self.meshes, self.coefs = [], []
         c = coef
         for l in range(n_levels):
@@ -115,7 +116,7 @@ class VarMultigrid:
         self.P = [prolongation(self.meshes[l], self.meshes[l + 1], sparse=True)
                   for l in range(n_levels - 1)]
         corr = corrections or [None] * n_levels
-        self.smoothers = [VarPatchSmoother(m, cf, mode, corrections=cr)
+        self.smoothers = [VarPatchSmoother(m, cf, mode, omega, corrections=cr)
                           for m, cf, cr in zip(self.meshes, self.coefs, corr)]
         inner0 = self.meshes[0].interior_nodes()
         self._inner0 = inner0

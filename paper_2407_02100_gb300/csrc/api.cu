@@ -75,6 +75,13 @@ bool valid_level(const gmg_problem* p, int level) {
 int apply_level(gmg_problem* p, int level, const void* x, void* y, const void* bvec, double alpha,
                 double beta) {
   const Level& L = p->levels[level];
+  if (p->varcoef) {
+    if (p->esize == 8)
+      return launch_apply_var<double>(L.g, L.n_elems, (const double*)x, (double*)y, (const double*)bvec,
+                                      alpha, beta, (const double*)p->coef[level], p->stream);
+    return launch_apply_var<float>(L.g, L.n_elems, (const float*)x, (float*)y, (const float*)bvec,
+                                   alpha, beta, (const float*)p->coef[level], p->stream);
+  }
   ApplyLaunch al;
   al.g = L.g;
   al.alpha = alpha;
@@ -117,7 +124,17 @@ int launch_colour(gmg_problem* p, const PatchLaunch& pl, void* u, const void* b)
 }
 
 int smooth_colour(gmg_problem* p, int level, void* u, const void* b, int colour) {
-  return launch_colour(p, colour_launch(p->levels[level], colour, p->desc.damping), u, b);
+  const PatchLaunch pl = colour_launch(p->levels[level], colour, p->desc.damping);
+  if (p->varcoef) {
+    if (pl.n_patches == 0) return GMG_OK;
+    const float* corr = p->local_solver == GMG_LOCAL_LEARNED ? p->corr[level] : nullptr;
+    if (p->esize == 8)
+      return launch_patch_var<double>(pl, (double*)u, (const double*)b, (const double*)p->coef[level],
+                                      (const double*)p->dinv, corr, p->corr_rank, p->stream);
+    return launch_patch_var<float>(pl, (float*)u, (const float*)b, (const float*)p->coef[level],
+                                   (const float*)p->dinv, corr, p->corr_rank, p->stream);
+  }
+  return launch_colour(p, pl, u, b);
 }
 
 int smooth(gmg_problem* p, int level, void* u, const void* b, int n_sweeps, int reverse) {
@@ -310,6 +327,11 @@ int restrict_to(gmg_problem* p, int fl, const void* fine, void* coarse) {
 
 int coarse_solve(gmg_problem* p, const void* b, void* x) {
   const LevelGeom& g = p->levels[0].g;
+  if (p->varcoef) {
+    if (p->esize == 8)
+      return launch_dense_solve<double>(g, p->coarse_inv, p->coarse_n, (const double*)b, (double*)x, p->stream);
+    return launch_dense_solve<float>(g, p->coarse_inv, p->coarse_n, (const float*)b, (float*)x, p->stream);
+  }
   const int dim = g.dim, m = p->m0;
   const int zero[3] = {0, 0, 0};
   const int one[3] = {1, 1, dim == 3 ? 1 : 0};
@@ -583,6 +605,10 @@ int gmg_apply_operator(gmg_problem* p, int level, const void* x, void* y) {
 int gmg_apply_operator_f64(gmg_problem* p, int level, const double* x, double* y) {
   if (!valid_level(p, level) || !x || !y || x == y) return GMG_ERR_INVALID_ARG;
   const Level& L = p->levels[level];
+  if (p->varcoef) {
+    if (level != (int)p->levels.size() - 1 || !p->coef64) return GMG_ERR_UNSUPPORTED;
+    return launch_apply_var<double>(L.g, L.n_elems, x, y, nullptr, op_scale(L), 0.0, p->coef64, p->stream);
+  }
   ApplyLaunch al;
   al.g = L.g;
   al.alpha = op_scale(L);
@@ -601,9 +627,80 @@ int gmg_smooth_colour(gmg_problem* p, int level, void* u, const void* b, int col
   return smooth_colour(p, level, u, b, colour);
 }
 
+int gmg_set_coefficient(gmg_problem* p, const double* coef) {
+  if (!p || !coef) return GMG_ERR_INVALID_ARG;
+  const int dim = p->desc.dim, k = p->desc.degree, L = (int)p->levels.size();
+  if (k > 3) return GMG_ERR_UNSUPPORTED;
+  const long long nfine = dim == 3 ? (long long)p->desc.n_cells * p->desc.n_cells * p->desc.n_cells
+                                   : (long long)p->desc.n_cells * p->desc.n_cells;
+  for (long long c = 0; c < nfine; ++c)
+    if (!(coef[c] > 0.0) || !std::isfinite(coef[c])) return GMG_ERR_INVALID_ARG;
+  // per-level coefficients: geometric mean of the 2^d children
+  std::vector<std::vector<double>> lev(L);
+  lev[L - 1].assign(coef, coef + nfine);
+  for (int l = L - 2; l >= 0; --l) {
+    const int n = p->levels[l].g.n, nf = p->levels[l + 1].g.n;
+    const long long nc = dim == 3 ? (long long)n * n * n : (long long)n * n;
+    lev[l].assign(nc, 0.0);
+    for (long long c = 0; c < nc; ++c) {
+      const int cx = (int)(c % n), cy = (int)((c / n) % n), cz = dim == 3 ? (int)(c / ((long long)n * n)) : 0;
+      double lg = 0.0;
+      for (int o = 0; o < (1 << dim); ++o) {
+        const int fx = 2 * cx + (o & 1), fy = 2 * cy + ((o >> 1) & 1), fz = dim == 3 ? 2 * cz + ((o >> 2) & 1) : 0;
+        lg += std::log(lev[l + 1][fx + (long long)nf * (fy + (long long)nf * fz)]);
+      }
+      lev[l][c] = std::exp(lg / (1 << dim));
+    }
+  }
+  // tables of the variable-coefficient kernels (unit cell, mirror FD)
+  const int m = 2 * k - 1;
+  std::vector<double> Mc, Kc, Mi, Ki, Tp, lp;
+  cell_matrices_1d(k, Mc, Kc);
+  assembled_1d(k, 2, 1, m, 1, m, Mi, Ki);
+  if (!generalized_eigen_mirror(m, Mi, Ki, Tp, lp)) return GMG_ERR_INVALID_ARG;
+  CHECK(upload_var_tables<double>(k, Mc.data(), Kc.data(), Tp.data()));
+  CHECK(upload_var_tables<float>(k, Mc.data(), Kc.data(), Tp.data()));
+  // dense inverse of the coarsest level's interior matrix
+  const int n0 = p->levels[0].g.n, m0 = n0 * k - 1;
+  const long long nint0 = dim == 3 ? (long long)m0 * m0 * m0 : (long long)m0 * m0;
+  if (nint0 > 2000) return GMG_ERR_UNSUPPORTED;
+  std::vector<double> A0, A0inv;
+  assemble_dense_var(dim, k, n0, lev[0].data(), A0);
+  if (!spd_inverse((int)nint0, A0, A0inv)) return GMG_ERR_INVALID_ARG;
+  // upload (problem precision per level; FP64 copies of the finest and the inverse)
+  const size_t es = p->esize;
+  p->esize = 8;
+  CHECK(upload_table(p, (void**)&p->coarse_inv, A0inv));
+  CHECK(upload_table(p, (void**)&p->coef64, lev[L - 1]));
+  p->esize = es;
+  p->coef.assign(L, nullptr);
+  for (int l = 0; l < L; ++l) CHECK(upload_table(p, &p->coef[l], lev[l]));
+  p->coarse_n = (int)nint0;
+  p->corr.assign(L, nullptr);
+  p->varcoef = true;
+  p->local_solver = GMG_LOCAL_FD_MEAN;
+  return cudaDeviceSynchronize() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+}
+
+int gmg_set_local_solver(gmg_problem* p, int solver) {
+  if (!p || !p->varcoef) return GMG_ERR_INVALID_ARG;
+  if (solver == GMG_LOCAL_FD_MEAN) {
+    p->local_solver = solver;
+    return GMG_OK;
+  }
+  if (solver == GMG_LOCAL_LEARNED) {
+    for (float* c : p->corr)
+      if (!c) return GMG_ERR_INVALID_ARG;  // train first
+    p->local_solver = solver;
+    return GMG_OK;
+  }
+  return GMG_ERR_INVALID_ARG;
+}
+
 int gmg_smooth_variant(gmg_problem* p, int level, void* u, const void* b, int variant,
                        long long batch_size, int reverse) {
   if (!valid_level(p, level) || !u || !b || u == b) return GMG_ERR_INVALID_ARG;
+  if (p->varcoef && variant != GMG_SWEEP_COMBINED) return GMG_ERR_UNSUPPORTED;
   switch (variant) {
     case GMG_SWEEP_COMBINED: return smooth(p, level, u, b, 1, reverse);
     case GMG_SWEEP_SEPARATED: return smooth_separated(p, level, u, b, reverse);
@@ -662,12 +759,18 @@ int cg_gmg_solve(gmg_problem* p, double* u, const double* b, double rtol, int ma
     if (st) *st = local;
     return status;
   };
+  // FP64 operator of the outer CG: y = sign A x + beta z
+  auto cg_apply = [&](const double* x, double* y, const double* z, double sign, double beta) -> int {
+    if (p->varcoef)
+      return launch_apply_var<double>(F.g, F.n_elems, x, y, z, sign * op_scale(F), beta, p->coef64, s);
+    ApplyLaunch al;
+    al.g = F.g;
+    al.alpha = sign * op_scale(F);
+    al.beta = beta;
+    return launch_apply<double>(al, x, y, z, s);
+  };
   // r = b - A u
-  ApplyLaunch al;
-  al.g = F.g;
-  al.alpha = -op_scale(F);
-  al.beta = 1.0;
-  CHECK(launch_apply<double>(al, u, p->cg_r, b, s));
+  CHECK(cg_apply(u, p->cg_r, b, -1.0, 1.0));
   CHECK(launch_dot(n, b, b, p->partial, sc + S_BB, s));
   CHECK(launch_dot(n, p->cg_r, p->cg_r, p->partial, sc + S_RR, s));
   CHECK(fetch());
@@ -686,10 +789,8 @@ int cg_gmg_solve(gmg_problem* p, double* u, const double* b, double rtol, int ma
   if (cudaMemcpyAsync(p->cg_p, p->cg_z, n * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return finish(GMG_ERR_CUDA);
   CHECK(launch_dot(n, p->cg_r, p->cg_z, p->partial, sc + S_RZ, s));
-  al.alpha = op_scale(F);
-  al.beta = 0.0;
   for (int it = 1; it <= max_it; ++it) {
-    CHECK(launch_apply<double>(al, p->cg_p, p->cg_q, nullptr, s));
+    CHECK(cg_apply(p->cg_p, p->cg_q, nullptr, 1.0, 0.0));
     CHECK(launch_dot(n, p->cg_p, p->cg_q, p->partial, sc + S_PQ, s));
     CHECK(launch_cg_update(n, u, p->cg_r, p->cg_p, p->cg_q, sc + S_RZ, sc + S_PQ, p->partial,
                            sc + S_RR, s));

@@ -102,6 +102,23 @@ int launch_patch_table(int dim, int k, const PatchLaunch* pls, T* const* us, con
 template <typename T>
 int launch_apply(const ApplyLaunch& al, const T* x, T* y, const T* bvec, cudaStream_t s);
 
+// Variable-coefficient kernels (var_f64.cu / var_f32.cu; degree <= 3).
+template <typename T>
+int upload_var_tables(int k, const double* Mc, const double* Kc, const double* That);
+// y = alpha sum_c a_c A_c x + beta bvec on interior nodes (bvec may be null)
+template <typename T>
+int launch_apply_var(const LevelGeom& g, long long n_elems, const T* x, T* y, const T* bvec,
+                     double alpha, double beta, const T* coef, cudaStream_t s);
+template <typename T>
+int launch_patch_var(const PatchLaunch& pl, T* u, const T* b, const T* coef, const T* dinv,
+                     const float* corr, int rank, cudaStream_t s);
+
+// x = Ainv b on the interior nodes of a level (Ainv dense FP64, interior
+// nodes numbered x fastest); the coarse solve of variable-coefficient problems
+template <typename T>
+int launch_dense_solve(const LevelGeom& g, const double* Ainv, int n_int, const T* b, T* x,
+                       cudaStream_t s);
+
 template <typename T>
 int launch_axis_op(const AxisOp& op, const T* in, T* out, const T* coef, cudaStream_t s);
 template <typename T>

@@ -63,6 +63,16 @@ struct gmg_problem {
   double* cg_q = nullptr;
   double* partial = nullptr;
   double* scal = nullptr;  // device scalars
+  // variable coefficient -div(a grad u) (gmg_set_coefficient): one value per
+  // cell and level (problem precision), the finest also in FP64 for the CG
+  bool varcoef = false;
+  std::vector<void*> coef;
+  double* coef64 = nullptr;
+  int local_solver = 0;             // GMG_LOCAL_FD_MEAN or GMG_LOCAL_LEARNED
+  int corr_rank = 0;
+  std::vector<float*> corr;         // per level: [patches][m^d * rank + rank] or null
+  double* coarse_inv = nullptr;     // dense inverse of the coarsest interior matrix
+  int coarse_n = 0;
   std::vector<void*> owned;
 };
 
@@ -89,6 +99,7 @@ int restrict_to(gmg_problem* p, int fl, const void* fine, void* coarse);
 int coarse_solve(gmg_problem* p, const void* b, void* x);
 int vcycle_level(gmg_problem* p, int l, void* x, const void* b);
 int create_problem(const gmg_desc* d, gmg_problem* p, const CreateOptions& opt);
+int upload_table(gmg_problem* p, void** dst, const std::vector<double>& src);
 int check_desc(const gmg_desc* d);
 
 }  // namespace detail

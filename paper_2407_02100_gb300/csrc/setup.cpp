@@ -259,6 +259,86 @@ bool generalized_eigen_mirror(int n, const std::vector<double>& M, const std::ve
   return true;
 }
 
+void assemble_dense_var(int dim, int k, int n, const double* coef, std::vector<double>& A) {
+  std::vector<double> Mc, Kc;
+  cell_matrices_1d(k, Mc, Kc);
+  const int N = n * k + 1, m = N - 2, E = k + 1;
+  const long long ni = dim == 3 ? (long long)m * m * m : (long long)m * m;
+  const double hs = dim == 3 ? 1.0 / n : 1.0;  // h^{d-2}
+  A.assign(ni * ni, 0.0);
+  const int nloc = dim == 3 ? E * E * E : E * E;
+  const long long ncell = dim == 3 ? (long long)n * n * n : (long long)n * n;
+  for (long long c = 0; c < ncell; ++c) {
+    const int cc[3] = {(int)(c % n), (int)((c / n) % n), dim == 3 ? (int)(c / ((long long)n * n)) : 0};
+    const double a = coef[c] * hs;
+    for (int pi = 0; pi < nloc; ++pi) {
+      const int li[3] = {pi % E, (pi / E) % E, dim == 3 ? pi / (E * E) : 0};
+      long long I = 0, stride = 1;
+      bool ok = true;
+      for (int d = 0; d < dim; ++d) {
+        const int g = cc[d] * k + li[d];
+        if (g < 1 || g > m) ok = false;
+        I += (g - 1) * stride;
+        stride *= m;
+      }
+      if (!ok) continue;
+      for (int pj = 0; pj < nloc; ++pj) {
+        const int lj[3] = {pj % E, (pj / E) % E, dim == 3 ? pj / (E * E) : 0};
+        long long J = 0, st2 = 1;
+        bool ok2 = true;
+        for (int d = 0; d < dim; ++d) {
+          const int g = cc[d] * k + lj[d];
+          if (g < 1 || g > m) ok2 = false;
+          J += (g - 1) * st2;
+          st2 *= m;
+        }
+        if (!ok2) continue;
+        double v = 0.0;
+        for (int al = 0; al < dim; ++al) {
+          double prod = 1.0;
+          for (int be = 0; be < dim; ++be) {
+            const std::vector<double>& Ed = (al == be) ? Kc : Mc;
+            prod *= Ed[li[be] * E + lj[be]];
+          }
+          v += prod;
+        }
+        A[I * ni + J] += a * v;
+      }
+    }
+  }
+}
+
+bool spd_inverse(int n, const std::vector<double>& A, std::vector<double>& Ainv) {
+  std::vector<double> L(A);
+  for (int j = 0; j < n; ++j) {
+    double d = L[(size_t)j * n + j];
+    for (int p = 0; p < j; ++p) d -= L[(size_t)j * n + p] * L[(size_t)j * n + p];
+    if (!(d > 0.0)) return false;
+    d = std::sqrt(d);
+    L[(size_t)j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double t = L[(size_t)i * n + j];
+      for (int p = 0; p < j; ++p) t -= L[(size_t)i * n + p] * L[(size_t)j * n + p];
+      L[(size_t)i * n + j] = t / d;
+    }
+  }
+  Ainv.assign((size_t)n * n, 0.0);
+  std::vector<double> y(n);
+  for (int c = 0; c < n; ++c) {  // solve L L^T x = e_c
+    for (int i = 0; i < n; ++i) {
+      double t = (i == c) ? 1.0 : 0.0;
+      for (int p = 0; p < i; ++p) t -= L[(size_t)i * n + p] * y[p];
+      y[i] = t / L[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double t = y[i];
+      for (int p = i + 1; p < n; ++p) t -= L[(size_t)p * n + i] * Ainv[(size_t)p * n + c];
+      Ainv[(size_t)i * n + c] = t / L[(size_t)i * n + i];
+    }
+  }
+  return true;
+}
+
 void prolongation_cell_1d(int k, std::vector<double>& P) {
   std::vector<double> xi = gauss_lobatto(k);
   P.assign((2 * k + 1) * (k + 1), 0.0);

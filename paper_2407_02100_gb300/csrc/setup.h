@@ -43,6 +43,14 @@ bool generalized_eigen(int n, const std::vector<double>& M, const std::vector<do
 bool generalized_eigen_mirror(int n, const std::vector<double>& M, const std::vector<double>& K,
                               std::vector<double>& T, std::vector<double>& lambda);
 
+// Interior stiffness matrix (dense, row-major, interior nodes x fastest) of
+// -div(a grad u) on a uniform mesh of n cells of width h = 1/n with one
+// coefficient per cell (coef: n^dim values, c_0 fastest).
+void assemble_dense_var(int dim, int k, int n, const double* coef, std::vector<double>& A);
+
+// Inverse of a symmetric positive definite matrix (Cholesky); false if not SPD.
+bool spd_inverse(int n, const std::vector<double>& A, std::vector<double>& Ainv);
+
 // Embedding prolongation of one coarse unit cell split in two fine cells:
 // P[r][p] = phi^coarse_p(x_r) for the 2k+1 fine nodes r of the coarse cell
 // ((2k+1) x (k+1), row-major).

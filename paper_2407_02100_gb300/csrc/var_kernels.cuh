@@ -1,0 +1,281 @@
+// Variable-coefficient kernels (-div(a grad u), one coefficient per cell),
+// for one scalar type GMG_T; included after patch_kernels.cuh (which gives
+// this translation unit its own __constant__ tables and FD helpers) by
+// var_f32.cu / var_f64.cu.
+//
+//  * apply_var_kernel: y += alpha * sum_c a_c A_c x_c, cell by cell by sum
+//    factorisation (App. A.1), accumulated with atomics (a node is shared
+//    by up to 2^d cells); the caller initialises y.
+//  * patch_var_kernel: one colour of the patch smoother (Algorithm 4) whose
+//    local residual is evaluated cell by cell with the cell coefficients
+//    (Sec. 3.1, eq. "main:4"), and whose local solver is the fast
+//    diagonalisation of the constant-coefficient patch scaled by the
+//    geometric mean abar of the 2^d cell coefficients, optionally plus a
+//    per-patch rank-R correction U diag(s) U^T (reference units):
+//        d = (1/abar) [ FD_ref(r_ref) + U diag(s) U^T r_ref ],  r_ref = h^{2-d} r.
+#pragma once
+#include "patch_kernels.cuh"
+
+namespace gmg {
+namespace GMG_NS {
+
+// one (K+1)-point 1D cell operator applied to a line: y_i = sum_j E[i][j] x_j
+template <int K, int KIND>
+__device__ __forceinline__ T cell1d(int i, const T (&x)[K + 1]) {
+  T acc = T(0);
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    const T e = KIND == 0 ? c_Mc[off_cell(K) + i * (K + 1) + j] : c_Kc[off_cell(K) + i * (K + 1) + j];
+    acc = fma(e, x[j], acc);
+  }
+  return acc;
+}
+
+// Cell operator (unit cell, coefficient 1) on an (K+1)^DIM block in shared
+// memory X (x fastest) -> OUT, using P, Q, A1, A2 as scratch; lines of `ncell`
+// cells (stride S between cells) are spread over NT threads.  Ends with a
+// barrier.
+template <int DIM, int K, int NT>
+__device__ __forceinline__ void cell_operator(T* X, T* P, T* Q, T* A1, T* A2, T* OUT, int ncell, int S) {
+  constexpr int E = K + 1;
+  if (DIM == 3) {
+    for (int idx = threadIdx.x; idx < ncell * E * E; idx += NT) {  // z: P = M_z x, Q = K_z x
+      const int c = idx / (E * E), l = idx % (E * E);
+      T v[E];
+#pragma unroll
+      for (int j = 0; j < E; ++j) v[j] = X[c * S + l + j * E * E];
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        P[c * S + l + i * E * E] = cell1d<K, 0>(i, v);
+        Q[c * S + l + i * E * E] = cell1d<K, 1>(i, v);
+      }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < ncell * E * E; idx += NT) {  // y: A1 = M_y P, A2 = K_y P + M_y Q
+      const int c = idx / (E * E), l = idx % (E * E);
+      const int x0 = l % E, z = l / E;
+      T p[E], q[E];
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        p[j] = P[c * S + x0 + j * E + z * E * E];
+        q[j] = Q[c * S + x0 + j * E + z * E * E];
+      }
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        A1[c * S + x0 + i * E + z * E * E] = cell1d<K, 0>(i, p);
+        A2[c * S + x0 + i * E + z * E * E] = cell1d<K, 1>(i, p) + cell1d<K, 0>(i, q);
+      }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < ncell * E * E; idx += NT) {  // x: OUT = K_x A1 + M_x A2
+      const int c = idx / (E * E), l = idx % (E * E);
+      T a1[E], a2[E];
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        a1[j] = A1[c * S + l * E + j];
+        a2[j] = A2[c * S + l * E + j];
+      }
+#pragma unroll
+      for (int i = 0; i < E; ++i) OUT[c * S + l * E + i] = cell1d<K, 1>(i, a1) + cell1d<K, 0>(i, a2);
+    }
+    __syncthreads();
+  } else {
+    for (int idx = threadIdx.x; idx < ncell * E; idx += NT) {  // y: P = M_y x, Q = K_y x
+      const int c = idx / E, l = idx % E;
+      T v[E];
+#pragma unroll
+      for (int j = 0; j < E; ++j) v[j] = X[c * S + l + j * E];
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        P[c * S + l + i * E] = cell1d<K, 0>(i, v);
+        Q[c * S + l + i * E] = cell1d<K, 1>(i, v);
+      }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < ncell * E; idx += NT) {  // x: OUT = K_x P + M_x Q
+      const int c = idx / E, l = idx % E;
+      T p[E], q[E];
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        p[j] = P[c * S + l * E + j];
+        q[j] = Q[c * S + l * E + j];
+      }
+#pragma unroll
+      for (int i = 0; i < E; ++i) OUT[c * S + l * E + i] = cell1d<K, 1>(i, p) + cell1d<K, 0>(i, q);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ void atomic_add(double* a, double v) { atomicAdd(a, v); }
+__device__ __forceinline__ void atomic_add(float* a, float v) { atomicAdd(a, v); }
+
+// y += alpha * sum_c a_c A_c x on the interior nodes (cells of unit width).
+template <int DIM, int K, int NT, int CPC>
+__global__ void __launch_bounds__(NT) apply_var_kernel(const T* __restrict__ x, T* __restrict__ y,
+                                                       const T* __restrict__ coef, LevelGeom g, T alpha) {
+  constexpr int E = K + 1;
+  constexpr int NE = DIM == 3 ? E * E * E : E * E;
+  __shared__ T X[CPC * NE], P[CPC * NE], Q[CPC * NE], A1[CPC * NE], A2[CPC * NE];
+  const int n = g.n, N = g.N;
+  const long long ncell = DIM == 3 ? (long long)n * n * n : (long long)n * n;
+  for (long long c0 = (long long)blockIdx.x * CPC; c0 < ncell; c0 += (long long)gridDim.x * CPC) {
+    const int nc = (int)(ncell - c0 < CPC ? ncell - c0 : CPC);
+    for (int idx = threadIdx.x; idx < nc * NE; idx += NT) {
+      const long long c = c0 + idx / NE;
+      const int t = idx % NE;
+      const int cx = (int)(c % n), cy = (int)((c / n) % n), cz = DIM == 3 ? (int)(c / ((long long)n * n)) : 0;
+      const int lx = t % E, ly = (t / E) % E, lz = DIM == 3 ? t / (E * E) : 0;
+      const long long gi = (long long)(cx * K + lx) + g.py * (cy * K + ly) + (DIM == 3 ? g.pz * (cz * K + lz) : 0);
+      X[idx] = x[gi];
+    }
+    __syncthreads();
+    cell_operator<DIM, K, NT>(X, P, Q, A1, A2, X, nc, NE);  // OUT overwrites X per line (own line only)
+    for (int idx = threadIdx.x; idx < nc * NE; idx += NT) {
+      const long long c = c0 + idx / NE;
+      const int t = idx % NE;
+      const int cx = (int)(c % n), cy = (int)((c / n) % n), cz = DIM == 3 ? (int)(c / ((long long)n * n)) : 0;
+      const int ix = cx * K + t % E, iy = cy * K + (t / E) % E, iz = DIM == 3 ? cz * K + t / (E * E) : 1;
+      if (ix <= 0 || ix >= N - 1 || iy <= 0 || iy >= N - 1 || (DIM == 3 && (iz <= 0 || iz >= N - 1))) continue;
+      const long long gi = ix + g.py * iy + (DIM == 3 ? g.pz * iz : 0);
+      atomic_add(y + gi, alpha * coef[c] * X[idx]);
+    }
+    __syncthreads();
+  }
+}
+
+// y = beta * b on interior nodes (b may be null: zero); padding untouched
+__global__ void init_interior_kernel(T* __restrict__ y, const T* __restrict__ b, T beta, LevelGeom g,
+                                     long long n_elems) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n_elems;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(e % g.py);
+    const int iy = (int)((e / g.py) % g.N);
+    const int iz = g.dim == 3 ? (int)(e / g.pz) : 1;
+    if (ix <= 0 || ix >= g.N - 1 || iy <= 0 || iy >= g.N - 1 || (g.dim == 3 && (iz <= 0 || iz >= g.N - 1)))
+      continue;
+    y[e] = b ? beta * b[e] : T(0);
+  }
+}
+
+// One colour of the variable-coefficient patch smoother, one patch per CTA.
+template <int DIM, int K, int NT>
+__global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const T* __restrict__ b,
+                                                       const T* __restrict__ coef,
+                                                       const T* __restrict__ dinv,
+                                                       const float* __restrict__ corr, int rank,
+                                                       PatchLaunch pl) {
+  constexpr int C = 2 * K + 1, M = 2 * K - 1, E = K + 1;
+  constexpr int NCLO = DIM == 3 ? C * C * C : C * C;
+  constexpr int NINT = DIM == 3 ? M * M * M : M * M;
+  constexpr int NE = DIM == 3 ? E * E * E : E * E;
+  constexpr int NCELL = 1 << DIM;
+  __shared__ T U[NCLO], R[NINT], RS[NINT], X[NE], P[NE], Q[NE], A1[NE], A2[NE];
+  __shared__ T s_coef[NCELL];
+  __shared__ T s_abar;
+  __shared__ float s_t[8];
+  const long long py = pl.g.py, pz = pl.g.pz;
+  const int n = pl.g.n;
+  const T sb = (T)pl.sb, om = (T)pl.omega;
+  for (int pid = blockIdx.x; pid < pl.n_patches; pid += gridDim.x) {
+    const int i0 = pid % pl.count[0];
+    const int rest = pid / pl.count[0];
+    const int i1 = rest % pl.count[1];
+    const int i2 = DIM == 3 ? rest / pl.count[1] : 0;
+    const int v0 = pl.first[0] + 2 * i0, v1 = pl.first[1] + 2 * i1, v2 = DIM == 3 ? pl.first[2] + 2 * i2 : 1;
+    const long long origin = (long long)(v0 - 1) * K + py * ((v1 - 1) * K) + (DIM == 3 ? pz * ((v2 - 1) * K) : 0);
+    for (int t = threadIdx.x; t < NCLO; t += NT) {
+      const int x = t % C, y = (t / C) % C, z = DIM == 3 ? t / (C * C) : 0;
+      U[t] = u[origin + x + py * y + pz * z];
+    }
+    for (int t = threadIdx.x; t < NINT; t += NT) {
+      const int x = t % M, y = (t / M) % M, z = DIM == 3 ? t / (M * M) : 0;
+      RS[t] = b[origin + 1 + x + py * (y + 1) + (DIM == 3 ? pz * (z + 1) : 0)];
+      R[t] = T(0);
+    }
+    if (threadIdx.x < NCELL) {
+      const int o0 = threadIdx.x & 1, o1 = (threadIdx.x >> 1) & 1, o2 = (threadIdx.x >> 2) & 1;
+      const long long c = (long long)(v0 - 1 + o0) + (long long)n * ((v1 - 1 + o1) + (DIM == 3 ? (long long)n * (v2 - 1 + o2) : 0));
+      s_coef[threadIdx.x] = coef[c];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      T lg = T(0);
+      for (int c = 0; c < NCELL; ++c) lg += log(s_coef[c]);
+      s_abar = exp(lg / (T)NCELL);
+    }
+    // ---- local residual cell by cell: R = sum_c a_c [A_c u_c]_interior ----
+    for (int c = 0; c < NCELL; ++c) {
+      const int o0 = c & 1, o1 = (c >> 1) & 1, o2 = (c >> 2) & 1;
+      for (int t = threadIdx.x; t < NE; t += NT) {
+        const int x = t % E, y = (t / E) % E, z = DIM == 3 ? t / (E * E) : 0;
+        X[t] = U[(o0 * K + x) + C * (o1 * K + y) + (DIM == 3 ? C * C * (o2 * K + z) : 0)];
+      }
+      __syncthreads();
+      cell_operator<DIM, K, NT>(X, P, Q, A1, A2, X, 1, NE);
+      const T ac = s_coef[c];
+      for (int t = threadIdx.x; t < NE; t += NT) {
+        const int px = o0 * K + t % E, py2 = o1 * K + (t / E) % E, pz2 = DIM == 3 ? o2 * K + t / (E * E) : 1;
+        if (px < 1 || px > M || py2 < 1 || py2 > M || (DIM == 3 && (pz2 < 1 || pz2 > M))) continue;
+        R[(px - 1) + M * (py2 - 1) + (DIM == 3 ? M * M * (pz2 - 1) : 0)] += ac * X[t];
+      }
+      __syncthreads();
+    }
+    // ---- reference residual r_ref = h^{2-d} b - R ----
+    for (int t = threadIdx.x; t < NINT; t += NT) {
+      const T r = sb * RS[t] - R[t];
+      RS[t] = r;
+      R[t] = r;
+    }
+    __syncthreads();
+    // ---- fast diagonalisation of the constant-coefficient patch ----
+    for (int a = 0; a < DIM; ++a) {
+      for (int l = threadIdx.x; l < (DIM == 3 ? M * M : M); l += NT) {
+        if (a == 0) fd_smem_line<K, true>(R + l * M, 1);
+        else if (a == 1) fd_smem_line<K, true>(R + (l % M) + (DIM == 3 ? (l / M) * M * M : 0), M);
+        else fd_smem_line<K, true>(R + l, M * M);
+      }
+      __syncthreads();
+    }
+    for (int t = threadIdx.x; t < NINT; t += NT) R[t] *= dinv[t];
+    __syncthreads();
+    for (int a = 0; a < DIM; ++a) {
+      for (int l = threadIdx.x; l < (DIM == 3 ? M * M : M); l += NT) {
+        if (a == 0) fd_smem_line<K, false>(R + l * M, 1);
+        else if (a == 1) fd_smem_line<K, false>(R + (l % M) + (DIM == 3 ? (l / M) * M * M : 0), M);
+        else fd_smem_line<K, false>(R + l, M * M);
+      }
+      __syncthreads();
+    }
+    // ---- learned rank-R correction U diag(s) U^T r_ref ----
+    if (corr) {
+      const int vid = (v0 - 1) + (n - 1) * ((v1 - 1) + (DIM == 3 ? (n - 1) * (v2 - 1) : 0));
+      const float* Up = corr + (long long)vid * (NINT * rank + rank);
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      for (int q = warp; q < rank; q += NT / 32) {
+        float acc = 0.f;
+        for (int i = lane; i < NINT; i += 32) acc += Up[i * rank + q] * (float)RS[i];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) s_t[q] = acc * Up[NINT * rank + q];
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < NINT; i += NT) {
+        float acc = 0.f;
+        for (int q = 0; q < rank; ++q) acc += Up[i * rank + q] * s_t[q];
+        R[i] += (T)acc;
+      }
+      __syncthreads();
+    }
+    // ---- scatter: u += omega d / abar ----
+    const T scale = om / s_abar;
+    for (int t = threadIdx.x; t < NINT; t += NT) {
+      const int x = t % M, y = (t / M) % M, z = DIM == 3 ? t / (M * M) : 0;
+      const long long gi = origin + 1 + x + py * (y + 1) + (DIM == 3 ? pz * (z + 1) : 0);
+      u[gi] = fma(scale, R[t], u[gi]);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace GMG_NS
+}  // namespace gmg

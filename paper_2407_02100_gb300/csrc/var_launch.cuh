@@ -1,0 +1,83 @@
+// Launchers of the variable-coefficient kernels for one scalar type;
+// included after var_kernels.cuh by var_f32.cu / var_f64.cu.
+#pragma once
+#include <algorithm>
+#include <vector>
+
+#include "../../include/gmg.h"
+
+namespace gmg {
+namespace GMG_NS {
+
+constexpr int kVarThreads = 128;
+template <int DIM, int K>
+struct VarCfg {
+  static constexpr int E = K + 1;
+  static constexpr int CPC = DIM == 3 ? 128 / (E * E) : 128 / E;  // cells per CTA of the operator
+};
+
+template <int DIM, int K>
+static int apply_var_impl(const LevelGeom& g, long long n_elems, const T* x, T* y, const T* bvec,
+                          double alpha, double beta, const T* coef, cudaStream_t s) {
+  init_interior_kernel<<<(int)std::min<long long>((n_elems + 255) / 256, 152LL * 16), 256, 0, s>>>(
+      y, bvec, (T)beta, g, n_elems);
+  count_launch();
+  constexpr int CPC = VarCfg<DIM, K>::CPC;
+  const long long ncell = DIM == 3 ? (long long)g.n * g.n * g.n : (long long)g.n * g.n;
+  const int grid = (int)std::min<long long>((ncell + CPC - 1) / CPC, 152LL * 32);
+  apply_var_kernel<DIM, K, kVarThreads, CPC><<<grid, kVarThreads, 0, s>>>(x, y, coef, g, (T)alpha);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+}
+
+template <int DIM, int K>
+static int patch_var_impl(const PatchLaunch& pl, T* u, const T* b, const T* coef, const T* dinv,
+                          const float* corr, int rank, cudaStream_t s) {
+  if (pl.n_patches <= 0) return GMG_OK;
+  const int grid = std::min(pl.n_patches, 152 * 16);
+  patch_var_kernel<DIM, K, kVarThreads><<<grid, kVarThreads, 0, s>>>(u, b, coef, dinv, corr, rank, pl);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+}
+
+#define GMG_VAR_DISPATCH(FN, DIMV, KV, ...)              \
+  switch ((DIMV) * 16 + (KV)) {                          \
+    case 2 * 16 + 1: return FN<2, 1>(__VA_ARGS__);       \
+    case 2 * 16 + 2: return FN<2, 2>(__VA_ARGS__);       \
+    case 2 * 16 + 3: return FN<2, 3>(__VA_ARGS__);       \
+    case 3 * 16 + 1: return FN<3, 1>(__VA_ARGS__);       \
+    case 3 * 16 + 2: return FN<3, 2>(__VA_ARGS__);       \
+    case 3 * 16 + 3: return FN<3, 3>(__VA_ARGS__);       \
+    default: return GMG_ERR_UNSUPPORTED;                 \
+  }
+
+}  // namespace GMG_NS
+
+template <>
+int upload_var_tables<GMG_T>(int k, const double* Mc, const double* Kc, const double* That) {
+  if (k < 1 || k > 8) return GMG_ERR_INVALID_ARG;
+  using namespace GMG_NS;
+  const int M = 2 * k - 1;
+  std::vector<T> mc((k + 1) * (k + 1)), kc((k + 1) * (k + 1)), tt(M * M);
+  for (int i = 0; i < (k + 1) * (k + 1); ++i) { mc[i] = (T)Mc[i]; kc[i] = (T)Kc[i]; }
+  for (int i = 0; i < M * M; ++i) tt[i] = (T)That[i];
+  cudaError_t e = cudaMemcpyToSymbol(c_Mc, mc.data(), mc.size() * sizeof(T), off_cell(k) * sizeof(T));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_Kc, kc.data(), kc.size() * sizeof(T), off_cell(k) * sizeof(T));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_T, tt.data(), tt.size() * sizeof(T), off_t(k) * sizeof(T));
+  return e == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+}
+
+template <>
+int launch_apply_var<GMG_T>(const LevelGeom& g, long long n_elems, const GMG_T* x, GMG_T* y,
+                            const GMG_T* bvec, double alpha, double beta, const GMG_T* coef,
+                            cudaStream_t s) {
+  GMG_VAR_DISPATCH(GMG_NS::apply_var_impl, g.dim, g.k, g, n_elems, x, y, bvec, alpha, beta, coef, s)
+}
+
+template <>
+int launch_patch_var<GMG_T>(const PatchLaunch& pl, GMG_T* u, const GMG_T* b, const GMG_T* coef,
+                            const GMG_T* dinv, const float* corr, int rank, cudaStream_t s) {
+  GMG_VAR_DISPATCH(GMG_NS::patch_var_impl, pl.g.dim, pl.g.k, pl, u, b, coef, dinv, corr, rank, s)
+}
+
+}  // namespace gmg

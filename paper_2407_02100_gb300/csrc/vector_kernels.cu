@@ -129,6 +129,23 @@ __global__ void cg_direction_kernel(long long n, double* __restrict__ p, const d
     p[i] = z[i] + beta * p[i];
 }
 
+// one warp per row of the dense inverse
+template <typename T>
+__global__ void dense_solve_kernel(LevelGeom g, const double* __restrict__ Ainv, int n_int,
+                                   const T* __restrict__ b, T* __restrict__ x) {
+  const int m = g.N - 2;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n_int) return;
+  auto node = [&](int i) -> long long {
+    const int ix = i % m + 1, iy = (i / m) % m + 1, iz = g.dim == 3 ? i / (m * m) + 1 : 0;
+    return ix + (long long)g.py * iy + (g.dim == 3 ? g.pz * iz : 0);
+  };
+  double acc = 0.0;
+  for (int j = lane; j < n_int; j += 32) acc += Ainv[(long long)warp * n_int + j] * (double)b[node(j)];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) x[node(warp)] = (T)acc;
+}
+
 constexpr int kSegThreads = 256;
 
 __global__ void seg_dot_kernel(Segments sg, const double* __restrict__ x, const double* __restrict__ y,
@@ -202,6 +219,17 @@ int launch_axis_op(const AxisOp& op, const T* in, T* out, const T* coef, cudaStr
 }
 template int launch_axis_op<double>(const AxisOp&, const double*, double*, const double*, cudaStream_t);
 template int launch_axis_op<float>(const AxisOp&, const float*, float*, const float*, cudaStream_t);
+
+template <typename T>
+int launch_dense_solve(const LevelGeom& g, const double* Ainv, int n_int, const T* b, T* x,
+                       cudaStream_t s) {
+  if (n_int <= 0) return GMG_OK;
+  const int threads = 256, blocks = (n_int * 32 + threads - 1) / threads;
+  dense_solve_kernel<T><<<blocks, threads, 0, s>>>(g, Ainv, n_int, b, x);
+  return status();
+}
+template int launch_dense_solve<double>(const LevelGeom&, const double*, int, const double*, double*, cudaStream_t);
+template int launch_dense_solve<float>(const LevelGeom&, const double*, int, const float*, float*, cudaStream_t);
 
 template <typename T>
 int launch_scale(long long n, T* x, const T* d, cudaStream_t s) {

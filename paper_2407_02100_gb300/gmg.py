@@ -29,7 +29,9 @@ EXPORTS = ["gmg_create", "gmg_destroy", "gmg_vector_layout", "gmg_level_info",
            "cg_gmg_solve", "gmg_patch_fd_1d", "gmg_kernel_launch_count", "gmg_status_string",
            "gmg_smooth_noalloc", "gmg_smooth_variant", "gmg_batch_create", "gmg_batch_destroy",
            "gmg_batch_layout", "gmg_batch_problem", "gmg_batch_smooth", "gmg_batch_vcycle",
-           "gmg_batch_cg_solve", "gmg_batch_autotune", "gmg_batch_set_ppc"]
+           "gmg_batch_cg_solve", "gmg_batch_autotune", "gmg_batch_set_ppc",
+           "gmg_set_coefficient", "gmg_set_local_solver"]
+GMG_LOCAL_FD_MEAN, GMG_LOCAL_LEARNED = 0, 1
 GMG_SWEEP_COMBINED, GMG_SWEEP_SEPARATED, GMG_SWEEP_BATCHED = 0, 1, 2
 
 
@@ -90,6 +92,8 @@ def lib():
             "gmg_batch_cg_solve": [vp, vp, vp, d, i, ctypes.POINTER(i), ctypes.POINTER(d)],
             "gmg_batch_autotune": [vp, ctypes.POINTER(i)],
             "gmg_batch_set_ppc": [vp, i],
+            "gmg_set_coefficient": [vp, vp],
+            "gmg_set_local_solver": [vp, i],
             "gmg_smooth_noalloc": [i, i, i, d, vp, vp, i, i, vp],
             "gmg_status_string": [i],
         }
@@ -209,6 +213,17 @@ def gmg_smooth_noalloc(dim, degree, n_cells, u, b, n_sweeps=1, reverse=False, da
     _check("gmg_smooth_noalloc", lib().gmg_smooth_noalloc(dim, degree, n_cells, damping, _ptr(u), _ptr(b),
                                                           n_sweeps, int(bool(reverse)),
                                                           ctypes.c_void_p(stream)))
+
+
+def gmg_set_coefficient(h, coef):
+    """coef: per-cell coefficients, numpy array of n^dim values (c_0 fastest
+    in C order, i.e. shape (n,)*dim indexed [c_{dim-1}, ..., c_0])."""
+    c = np.ascontiguousarray(np.asarray(coef, dtype=np.float64).ravel())
+    _check("gmg_set_coefficient", lib().gmg_set_coefficient(h, c.ctypes.data_as(ctypes.c_void_p)))
+
+
+def gmg_set_local_solver(h, solver):
+    _check("gmg_set_local_solver", lib().gmg_set_local_solver(h, solver))
 
 
 def gmg_kernel_launch_count():
