@@ -270,6 +270,44 @@ int gmg_set_coefficient(gmg_problem* p, const double* coef);
  * completed gmg_learned_train. */
 int gmg_set_local_solver(gmg_problem* p, int solver);
 
+/* ---- Learned correction of the local solver (no counterpart in the paper;
+ * it builds on the paper's remark that approximate local solvers fit the
+ * subspace-correction framework, Sec. 2.1).  Variable-coefficient problems,
+ * degree <= 3 in 3D (patch interiors of at most 125 nodes).
+ * A two-layer perceptron (8 -> 32 tanh -> m^d R + R, R = 4) maps the
+ * log-coefficients of a patch's cells, relative to their mean, to a
+ * symmetric rank-R correction U diag(s) U^T of the reference FD inverse.
+ * gmg_learned_train generates its data by exact dense (Cholesky, FP64) solves
+ * of the sample patches of the finest level -- sample_vertices: HOST array of
+ * n_samples lexicographic vertex ids v0-1 + (n-1)(v1-1) [+ (n-1)^2 (v2-1)];
+ * residuals: DEVICE array n_samples x m^d (FP64) of reference-unit residuals --
+ * trains with Adam for `steps` minibatches of `batch` samples (learning rate
+ * lr; parameters initialised from `seed`; FP32 master weights) with the loss
+ * ||FD r + U diag(s) U^T r - A_exact^{-1} r||^2 / ||A_exact^{-1} r||^2, then
+ * evaluates the network (FP16-rounded weights, FP32 accumulation) on every
+ * patch of every level and keeps a patch's correction only if it lowers the
+ * local energy-norm error on a probe residual (plain FD is the fallback).
+ * loss_history (HOST, `steps` entries) and kept_patches may be NULL.  On
+ * success the local solver becomes GMG_LOCAL_LEARNED.  Allocates the
+ * per-patch corrections (m^d R + R floats per patch and level). */
+int gmg_learned_train(gmg_problem* p, int n_samples, const int* sample_vertices,
+                      const double* residuals, int steps, int batch, double lr, unsigned seed,
+                      double* loss_history, int* kept_patches);
+
+/* Copy the per-patch corrections of `level` (patches in lexicographic vertex
+ * order, each U (m^d x R, row-major) then s (R)) to the HOST array out of
+ * `count` floats. */
+int gmg_learned_corrections(const gmg_problem* p, int level, float* out, long long count);
+
+/* Loss and gradient of the perceptron on one batch (for testing the kernels):
+ * params (DEVICE, FP32) = W1 [hidden x 2^dim] | b1 [hidden] | W2 [no x hidden]
+ * | b2 [no] with no = m^dim rank + rank; X (DEVICE FP32, n x 2^dim); R, DFD,
+ * DEX (DEVICE FP64, n x m^dim); loss -> HOST double; grads (DEVICE FP32, same
+ * layout as params).  rank <= 4, hidden <= 32, degree <= 3. */
+int gmg_mlp_loss_grad(int dim, int degree, int rank, int hidden, int n, const float* params,
+                      const float* X, const double* R, const double* DFD, const double* DEX,
+                      double* loss, float* grads);
+
 /* Host-only set-up math exposed for testing: the 1D fast-diagonalisation
  * data of one vertex patch built from two cells of unit width (App. A.3):
  * M, K = interior (2k-1)x(2k-1) mass and stiffness of the two-cell 1D

@@ -30,7 +30,8 @@ EXPORTS = ["gmg_create", "gmg_destroy", "gmg_vector_layout", "gmg_level_info",
            "gmg_smooth_noalloc", "gmg_smooth_variant", "gmg_batch_create", "gmg_batch_destroy",
            "gmg_batch_layout", "gmg_batch_problem", "gmg_batch_smooth", "gmg_batch_vcycle",
            "gmg_batch_cg_solve", "gmg_batch_autotune", "gmg_batch_set_ppc",
-           "gmg_set_coefficient", "gmg_set_local_solver"]
+           "gmg_set_coefficient", "gmg_set_local_solver", "gmg_learned_train",
+           "gmg_learned_corrections", "gmg_mlp_loss_grad"]
 GMG_LOCAL_FD_MEAN, GMG_LOCAL_LEARNED = 0, 1
 GMG_SWEEP_COMBINED, GMG_SWEEP_SEPARATED, GMG_SWEEP_BATCHED = 0, 1, 2
 
@@ -94,6 +95,10 @@ def lib():
             "gmg_batch_set_ppc": [vp, i],
             "gmg_set_coefficient": [vp, vp],
             "gmg_set_local_solver": [vp, i],
+            "gmg_learned_train": [vp, i, ctypes.POINTER(i), vp, i, i, d, ctypes.c_uint,
+                                  ctypes.POINTER(d), ctypes.POINTER(i)],
+            "gmg_learned_corrections": [vp, i, vp, ll],
+            "gmg_mlp_loss_grad": [i, i, i, i, i, vp, vp, vp, vp, vp, ctypes.POINTER(d), vp],
             "gmg_smooth_noalloc": [i, i, i, d, vp, vp, i, i, vp],
             "gmg_status_string": [i],
         }
@@ -224,6 +229,37 @@ def gmg_set_coefficient(h, coef):
 
 def gmg_set_local_solver(h, solver):
     _check("gmg_set_local_solver", lib().gmg_set_local_solver(h, solver))
+
+
+def gmg_learned_train(h, sample_vertices, residuals, steps=300, batch=1024, lr=3e-3, seed=0):
+    """sample_vertices: host int array; residuals: CUDA float64 tensor
+    [n_samples, m^d].  Returns (loss history, kept patch count)."""
+    verts = np.ascontiguousarray(np.asarray(sample_vertices, dtype=np.int32))
+    hist = (ctypes.c_double * max(steps, 1))()
+    kept = ctypes.c_int()
+    _check("gmg_learned_train", lib().gmg_learned_train(
+        h, len(verts), verts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _ptr(residuals), steps, batch,
+        lr, seed, hist, ctypes.byref(kept)))
+    return list(hist)[:steps], kept.value
+
+
+def gmg_learned_corrections(h, level, n_patches, per_patch):
+    out = np.zeros(n_patches * per_patch, dtype=np.float32)
+    _check("gmg_learned_corrections", lib().gmg_learned_corrections(
+        h, level, out.ctypes.data_as(ctypes.c_void_p), out.size))
+    return out.reshape(n_patches, per_patch)
+
+
+def gmg_mlp_loss_grad(dim, degree, rank, hidden, params, X, R, DFD, DEX):
+    """All arrays CUDA tensors (params, X float32; R, DFD, DEX float64).
+    Returns (loss, grads tensor)."""
+    import torch
+    grads = torch.zeros_like(params)
+    loss = ctypes.c_double()
+    _check("gmg_mlp_loss_grad", lib().gmg_mlp_loss_grad(
+        dim, degree, rank, hidden, X.shape[0], _ptr(params), _ptr(X), _ptr(R), _ptr(DFD), _ptr(DEX),
+        ctypes.byref(loss), _ptr(grads)))
+    return loss.value, grads
 
 
 def gmg_kernel_launch_count():

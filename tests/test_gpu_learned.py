@@ -1,0 +1,100 @@
+"""The learned correction of the local solver: the CUDA training kernels'
+gradients against the oracle's analytic FP64 gradients, training reduces the
+local-solve loss, the corrected smoother reproduces the oracle's smoother
+given the same per-patch corrections, and the trained network gains over
+plain mean-coefficient FD (fewer PCG iterations)."""
+import numpy as np
+import pytest
+
+from oracle import learned
+from oracle.mesh import Mesh
+from oracle.varcoef import VarPatchSmoother
+from paper_2407_02100_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gmg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2407_02100_gb300 import build, gmg as g
+    build.build()
+    return g
+
+
+@pytest.mark.parametrize("dim,k,rank,nh", [(3, 2, 4, 8), (2, 3, 3, 32), (3, 3, 4, 32)])
+def test_gradients_match_oracle(gmg, dim, k, rank, nh):
+    import torch
+    rng = np.random.default_rng(dim * 10 + k)
+    nf, nint, N = 2 ** dim, (2 * k - 1) ** dim, 24
+    no = nint * rank + rank
+    params = [0.3 * rng.standard_normal((nh, nf)), 0.1 * rng.standard_normal(nh),
+              0.3 * rng.standard_normal((no, nh)), 0.1 * rng.standard_normal(no)]
+    params = [p.astype(np.float32).astype(np.float64) for p in params]
+    X = rng.standard_normal((N, nf)).astype(np.float32).astype(np.float64)
+    R, DFD, DEX = (rng.standard_normal((N, nint)) for _ in range(3))
+    L, grads = learned.loss_and_grads(params, X, R, DFD, DEX, rank)
+    flat = np.concatenate([p.ravel() for p in params])
+    cuda = lambda a, t=torch.float64: torch.tensor(a, dtype=t, device="cuda")
+    Lg, g = gmg.gmg_mlp_loss_grad(dim, k, rank, nh, cuda(flat, torch.float32), cuda(X, torch.float32),
+                                  cuda(R), cuda(DFD), cuda(DEX))
+    gref = np.concatenate([x.ravel() for x in grads])
+    assert abs(Lg - L) <= 1e-5 * abs(L)
+    assert np.linalg.norm(g.cpu().numpy() - gref) <= 1e-4 * np.linalg.norm(gref)
+
+
+def _train(gmg, P, dim, k, n, steps=300, seed=0):
+    import torch
+    nint = (2 * k - 1) ** dim
+    npatch = (n - 1) ** dim
+    verts = np.random.default_rng(seed + 1).permutation(npatch)
+    res = torch.tensor(np.random.default_rng(seed + 2).standard_normal((npatch, nint)), device="cuda")
+    return gmg.gmg_learned_train(P.h, verts, res, steps=steps, batch=min(1024, npatch), lr=3e-3, seed=seed)
+
+
+def test_training_reduces_loss_and_sweep_matches_oracle(gmg):
+    dim, k, n = 3, 2, 6
+    coef = inputs.lognormal_coefficient(dim, n, 31, sigma=0.5)
+    P = gmg.Problem(dim, k, n, n_levels=1)
+    gmg.gmg_set_coefficient(P.h, coef)
+    hist, kept = _train(gmg, P, dim, k, n)
+    assert hist[-1] < 0.8 * hist[0], (hist[0], hist[-1])
+    npatch, nint, rank = (n - 1) ** dim, (2 * k - 1) ** dim, 4
+    assert 0 < kept <= npatch
+    C = gmg.gmg_learned_corrections(P.h, 0, npatch, nint * rank + rank).astype(np.float64)
+    corr = {}
+    for vid in range(npatch):
+        v = (vid % (n - 1) + 1, (vid // (n - 1)) % (n - 1) + 1, vid // (n - 1) ** 2 + 1)
+        corr[v] = (C[vid, :nint * rank].reshape(nint, rank), C[vid, nint * rank:])
+    m = Mesh(dim, k, n)
+    u0 = inputs.random_nodal(dim, k, n, 32)
+    b = inputs.random_nodal(dim, k, n, 33)
+    ud = P.to_device(u0)
+    gmg.gmg_smooth(P.h, 0, ud, P.to_device(b), 1, False)
+    ref = VarPatchSmoother(m, coef, "learned", corrections=corr).sweep(u0, b)
+    got = P.from_device(ud)
+    # the correction is applied in FP32 on the GPU (FP16-rounded network)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-6
+
+
+def test_learned_correction_gains_over_plain_fd(gmg):
+    """2D Q2 32^2, lognormal coefficient (sigma 1, correlation length 0.1):
+    the corrected local solver needs fewer PCG iterations than plain
+    mean-coefficient FD at the same damping."""
+    import torch
+    dim, k, n, L = 2, 2, 32, 3
+    coef = inputs.lognormal_coefficient(dim, n, 21)
+    b = inputs.random_nodal(dim, k, n, 22)
+    its = {}
+    for mode in ("fd", "learned"):
+        P = gmg.Problem(dim, k, n, n_levels=L)
+        gmg.gmg_set_coefficient(P.h, coef)
+        if mode == "learned":
+            hist, kept = _train(gmg, P, dim, k, n)
+            assert hist[-1] < 0.6 * hist[0]
+        u = P.zeros(dtype=torch.float64)
+        _, st = gmg.cg_gmg_solve(P.h, u, P.to_device(b, dtype=torch.float64), 1e-10, 200)
+        its[mode] = st.iterations
+    assert its["learned"] < its["fd"], its
