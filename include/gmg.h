@@ -278,15 +278,18 @@ int gmg_set_local_solver(gmg_problem* p, int solver);
  * log-coefficients of a patch's cells, relative to their mean, to a
  * symmetric rank-R correction U diag(s) U^T of the reference FD inverse.
  * gmg_learned_train generates its data by exact dense (Cholesky, FP64) solves
- * of the sample patches of the finest level -- sample_vertices: HOST array of
- * n_samples lexicographic vertex ids v0-1 + (n-1)(v1-1) [+ (n-1)^2 (v2-1)];
+ * of sample patches of any level -- sample_vertices: HOST array of n_samples
+ * patch ids over the levels, finest level first: ids [0, (n-1)^d) are the
+ * finest level's lexicographic vertex ids v0-1 + (n-1)(v1-1) [+ (n-1)^2 (v2-1)],
+ * the next (n/2-1)^d ids those of the next coarser level, and so on;
  * residuals: DEVICE array n_samples x m^d (FP64) of reference-unit residuals --
  * trains with Adam for `steps` minibatches of `batch` samples (learning rate
  * lr; parameters initialised from `seed`; FP32 master weights) with the loss
- * ||FD r + U diag(s) U^T r - A_exact^{-1} r||^2 / ||A_exact^{-1} r||^2, then
+ * ||theta FD r + U diag(s) U^T r - A_exact^{-1} r||^2 / ||A_exact^{-1} r||^2
+ * (theta = min(1, 1.8 abar / max_c a_c), the FD damping of the patch), then
  * evaluates the network (FP16-rounded weights, FP32 accumulation) on every
  * patch of every level and keeps a patch's correction only if it lowers the
- * local energy-norm error on a probe residual (plain FD is the fallback).
+ * local energy-norm error on a probe residual (damped FD is the fallback).
  * loss_history (HOST, `steps` entries) and kept_patches may be NULL.  On
  * success the local solver becomes GMG_LOCAL_LEARNED.  Allocates the
  * per-patch corrections (m^d R + R floats per patch and level). */

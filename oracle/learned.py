@@ -5,9 +5,11 @@ Model (a two-layer perceptron, our design; the paper has none):
   features  x = log a_c - mean_c log a_c over the 2^d cells of a patch
   hidden    h = tanh(W1 x + b1)
   output    o = W2 h + b2,  U[i, q] = o[i * R + q] (i < m^d, q < R), s[q] = o[m^d R + q]
-  solve     d = Ahat^{-1} r  +  U diag(s) U^T r     (reference units, coefficient a/abar)
+  solve     d = theta Ahat^{-1} r  +  U diag(s) U^T r   (reference units, coefficient
+            w = a/abar; theta = min(1, 1.8 / max_c w_c), the FD damping)
 Loss per sample: ||d - d_exact||^2 / ||d_exact||^2, averaged over the batch,
-with d_exact the exact solve with the normalised patch matrix.
+with d_exact the exact solve with the normalised patch matrix; DFD holds the
+damped FD term theta Ahat^{-1} r.
 """
 import numpy as np
 

@@ -6,12 +6,19 @@ covered by the framework although P_j then stops being a projection) is applied
 with three local solvers:
   exact       A_j^{-1} by dense LU of the patch block assembled from the 2^d
               cell matrices scaled by their coefficients;
-  fd_mean     (1/abar) Ahat_j^{-1}: the constant-coefficient patch inverse
-              (fast diagonalisation, App. A.3) scaled by the geometric mean
-              abar of the 2^d cell coefficients (our reading of how to use
-              fast diagonalisation when it is only approximate);
-  learned     fd_mean plus a rank-r symmetric correction U diag(s) U^T in the
-              same scaling, (U, s) given per patch (from the MLP).
+  fd_mean     theta_j (1/abar) Ahat_j^{-1}: the constant-coefficient patch
+              inverse (fast diagonalisation, App. A.3) scaled by the geometric
+              mean abar of the 2^d cell coefficients, with the per-patch
+              damping theta_j = min(1, 1.8 abar / max_c a_c).  Since
+              A_j <= max_c a_c Ahat_j, theta_j bounds the spectrum of the
+              damped local update by 1.8 < 2, so every patch correction
+              decreases the energy (our reading of how to use fast
+              diagonalisation when it is only approximate);
+  learned     (1/abar) (theta_j Ahat_j^{-1} + U diag(s) U^T): the damped FD
+              inverse plus a rank-r symmetric correction given per patch (from
+              the MLP, trained so that the sum approximates the exact patch
+              inverse; a patch whose correction is gated off keeps s = 0,
+              i.e. damped FD).
 Coarse levels use the geometric mean of the 2^d children as cell coefficient
 (our reading; the paper's test problem has constant coefficients).
 """
@@ -64,14 +71,15 @@ class VarPatchSmoother:
             cc = patch_cell_coefs(self.mesh, self.coef, v)
             Abar, inner = self.mesh.patch_block(cc)
             abar = np.exp(np.mean(np.log(cc)))
-            self._cache[key] = (Abar, sla.lu_factor(Abar[:, inner]), abar)
+            theta = min(1.0, 1.8 * abar / np.max(cc))
+            self._cache[key] = (Abar, sla.lu_factor(Abar[:, inner]), abar, theta)
         return self._cache[key]
 
     def local_solve(self, v, r):
-        Abar, lu, abar = self._patch(v)
+        Abar, lu, abar, theta = self._patch(v)
         if self.mode == "exact":
             return sla.lu_solve(lu, r)
-        d = self.ref_inv @ (self.hscale * r)
+        d = theta * (self.ref_inv @ (self.hscale * r))
         if self.mode == "learned":
             U, s = self.corrections[tuple(int(x) for x in v)]
             d = d + U @ (s * (U.T @ (self.hscale * r)))
@@ -82,7 +90,7 @@ class VarPatchSmoother:
         V = m.vertices_of_colour(c)
         updates = []
         for v in V:
-            Abar, _, _ = self._patch(v)
+            Abar = self._patch(v)[0]
             clo = m.closure_index(v[None, :])[0]
             inn = m.interior_index(v[None, :])[0]
             r = b[inn] - Abar @ u[clo]

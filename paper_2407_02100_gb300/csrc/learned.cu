@@ -6,10 +6,11 @@
 // For a patch with cell coefficients a_c, normalised w_c = a_c / abar
 // (abar = geometric mean), the exact reference-unit local inverse is
 // Ahat(w)^{-1}; plain FD uses Ahat(1)^{-1}.  A two-layer perceptron maps the
-// features x_c = log w_c to a symmetric rank-R correction U diag(s) U^T:
+// features x_c = log w_c to a symmetric rank-R correction U diag(s) U^T of
+// the damped FD inverse theta Ahat(1)^{-1}, theta = min(1, 1.8 / max_c w_c):
 //     h = tanh(W1 x + b1),  o = W2 h + b2,  U[i][q] = o[i R + q],  s[q] = o[m^d R + q]
 // trained on exact patch solves generated here (dense Cholesky per patch,
-// FP64) with the loss ||FD r + U diag(s) U^T r - Ahat(w)^{-1} r||^2 / ||Ahat(w)^{-1} r||^2.
+// FP64) with the loss ||theta FD r + U diag(s) U^T r - Ahat(w)^{-1} r||^2 / ||Ahat(w)^{-1} r||^2.
 // Training runs on the GPU with these kernels (forward, loss gradient,
 // backward, Adam), master weights FP32; inference uses FP16-rounded weights
 // with FP32 accumulation.  Plain FD stays the fallback and the judge: after
@@ -71,7 +72,7 @@ __device__ __forceinline__ double emb(bool stiff, int o, int k, int i, int j) {
 }
 
 // Exact reference solve of one patch per CTA: assemble Ahat(w) densely,
-// Cholesky in shared memory, solve for r.  Outputs d_ex and d_fd = FD r
+// Cholesky in shared memory, solve for r.  Outputs d_ex and d_fd = theta FD r
 // (FD by dense tensor application of T diag(dinv) T^T).  When `corr` is given
 // (gate mode), compares the energy-norm errors of FD and FD + correction and
 // zeroes the correction's s entries if it does not help.
@@ -94,6 +95,9 @@ __global__ void exact_patch_kernel(Shape sh, int n, const double* __restrict__ W
     if (threadIdx.x < sh.ncell) s_w[threadIdx.x] = W[(long long)smp * sh.ncell + threadIdx.x];
     for (int i = threadIdx.x; i < N; i += blockDim.x) r[i] = R[(long long)smp * N + i];
     __syncthreads();
+    double wmax = s_w[0];
+    for (int o = 1; o < sh.ncell; ++o) wmax = fmax(wmax, s_w[o]);
+    const double theta = fmin(1.0, 1.8 / wmax);  // the FD damping (w has geometric mean 1)
     // ---- assemble Ahat(w) ----
     for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
       const int I = idx / N, J = idx % N;
@@ -163,7 +167,7 @@ __global__ void exact_patch_kernel(Shape sh, int n, const double* __restrict__ W
         if (dim == 3) w *= l_T[i2 * m + j2];
         acc += w * t[j];
       }
-      e1[i] = acc;  // d_fd
+      e1[i] = acc * theta;  // d_fd
     }
     __syncthreads();
     if (DEX)
@@ -520,15 +524,41 @@ int gmg_learned_train(gmg_problem* p, int n_samples, const int* sample_vertices,
   double* dinv = buf.get<double>(sh.nint);
   if (!dinv || cudaMemcpy(dinv, dinv_h.data(), sh.nint * 8, cudaMemcpyHostToDevice) != cudaSuccess)
     return GMG_ERR_CUDA;
-  // ---- training data: exact solves of the sample patches (finest level) ----
-  const int nfin = p->levels[L - 1].g.n;
-  const int npatch_f = dim == 3 ? (nfin - 1) * (nfin - 1) * (nfin - 1) : (nfin - 1) * (nfin - 1);
-  std::vector<int> verts(sample_vertices, sample_vertices + n_samples);
-  for (int v : verts)
-    if (v < 0 || v >= npatch_f) return GMG_ERR_INVALID_ARG;
-  std::vector<float> Xh;
-  std::vector<double> Wh;
-  patch_features(lev[L - 1], dim, nfin, verts, Xh, Wh);
+  // ---- training data: exact solves of the sample patches; sample ids run
+  // over the patches of all levels, finest level first ----
+  std::vector<long long> first(L + 1, 0);  // first id of level l; first[L] = total
+  {
+    long long acc = 0;
+    for (int l = L - 1; l >= 0; --l) {
+      const long long nl = p->levels[l].g.n - 1;
+      first[l] = acc;
+      acc += dim == 3 ? nl * nl * nl : nl * nl;
+    }
+    first[L] = acc;  // total
+  }
+  for (int i = 0; i < n_samples; ++i)
+    if (sample_vertices[i] < 0 || sample_vertices[i] >= first[L]) return GMG_ERR_INVALID_ARG;
+  std::vector<float> Xh((size_t)n_samples * sh.nf);
+  std::vector<double> Wh((size_t)n_samples * sh.nf);
+  for (int l = 0; l < L; ++l) {
+    const long long lo = first[l];
+    std::vector<int> idx, vl;
+    const long long nl = p->levels[l].g.n - 1, cnt = dim == 3 ? nl * nl * nl : nl * nl;
+    for (int i = 0; i < n_samples; ++i)
+      if (sample_vertices[i] >= lo && sample_vertices[i] < lo + cnt) {
+        idx.push_back(i);
+        vl.push_back((int)(sample_vertices[i] - lo));
+      }
+    if (idx.empty()) continue;
+    std::vector<float> Xl;
+    std::vector<double> Wl;
+    patch_features(lev[l], dim, p->levels[l].g.n, vl, Xl, Wl);
+    for (size_t j = 0; j < idx.size(); ++j)
+      for (int c = 0; c < sh.nf; ++c) {
+        Xh[(size_t)idx[j] * sh.nf + c] = Xl[j * sh.nf + c];
+        Wh[(size_t)idx[j] * sh.nf + c] = Wl[j * sh.nf + c];
+      }
+  }
   float* X = buf.get<float>(Xh.size());
   double* W = buf.get<double>(Wh.size());
   double* DEX = buf.get<double>((size_t)n_samples * sh.nint);

@@ -11,8 +11,11 @@
 //    (Sec. 3.1, eq. "main:4"), and whose local solver is the fast
 //    diagonalisation of the constant-coefficient patch scaled by the
 //    geometric mean abar of the 2^d cell coefficients, optionally plus a
-//    per-patch rank-R correction U diag(s) U^T (reference units):
-//        d = (1/abar) [ FD_ref(r_ref) + U diag(s) U^T r_ref ],  r_ref = h^{2-d} r.
+//    per-patch rank-R correction U diag(s) U^T (reference units); the FD term
+//    is damped per patch by theta = min(1, 1.8 abar / max_c a_c)
+//    (A_j <= max_c a_c Ahat_j, so the damped FD update's spectrum stays
+//    below 1.8), the learned term approximates the rest of the exact inverse:
+//        d = (1/abar) [ theta FD_ref(r_ref) + U diag(s) U^T r_ref ],  r_ref = h^{2-d} r.
 #pragma once
 #include "patch_kernels.cuh"
 
@@ -172,7 +175,7 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
   constexpr int NCELL = 1 << DIM;
   __shared__ T U[NCLO], R[NINT], RS[NINT], X[NE], P[NE], Q[NE], A1[NE], A2[NE];
   __shared__ T s_coef[NCELL];
-  __shared__ T s_abar;
+  __shared__ T s_abar, s_theta;
   __shared__ float s_t[8];
   const long long py = pl.g.py, pz = pl.g.pz;
   const int n = pl.g.n;
@@ -200,9 +203,14 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      T lg = T(0);
-      for (int c = 0; c < NCELL; ++c) lg += log(s_coef[c]);
-      s_abar = exp(lg / (T)NCELL);
+      T lg = T(0), amax = s_coef[0];
+      for (int c = 0; c < NCELL; ++c) {
+        lg += log(s_coef[c]);
+        amax = max(amax, s_coef[c]);
+      }
+      const T abar = exp(lg / (T)NCELL);
+      s_abar = abar;
+      s_theta = min(T(1), T(1.8) * abar / amax);
     }
     // ---- local residual cell by cell: R = sum_c a_c [A_c u_c]_interior ----
     for (int c = 0; c < NCELL; ++c) {
@@ -262,12 +270,12 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
       for (int i = threadIdx.x; i < NINT; i += NT) {
         float acc = 0.f;
         for (int q = 0; q < rank; ++q) acc += Up[i * rank + q] * s_t[q];
-        R[i] += (T)acc;
+        R[i] = fma(s_theta, R[i], (T)acc);
       }
       __syncthreads();
     }
     // ---- scatter: u += omega d / abar ----
-    const T scale = om / s_abar;
+    const T scale = corr ? om / s_abar : om * s_theta / s_abar;
     for (int t = threadIdx.x; t < NINT; t += NT) {
       const int x = t % M, y = (t / M) % M, z = DIM == 3 ? t / (M * M) : 0;
       const long long gi = origin + 1 + x + py * (y + 1) + (DIM == 3 ? pz * (z + 1) : 0);

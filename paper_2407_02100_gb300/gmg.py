@@ -232,7 +232,8 @@ def gmg_set_local_solver(h, solver):
 
 
 def gmg_learned_train(h, sample_vertices, residuals, steps=300, batch=1024, lr=3e-3, seed=0):
-    """sample_vertices: host int array; residuals: CUDA float64 tensor
+    """sample_vertices: host int array of patch ids over all levels, finest
+    level first (see learned_patch_count); residuals: CUDA float64 tensor
     [n_samples, m^d].  Returns (loss history, kept patch count)."""
     verts = np.ascontiguousarray(np.asarray(sample_vertices, dtype=np.int32))
     hist = (ctypes.c_double * max(steps, 1))()
@@ -241,6 +242,12 @@ def gmg_learned_train(h, sample_vertices, residuals, steps=300, batch=1024, lr=3
         h, len(verts), verts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _ptr(residuals), steps, batch,
         lr, seed, hist, ctypes.byref(kept)))
     return list(hist)[:steps], kept.value
+
+
+def learned_patch_count(dim, n_cells, n_levels):
+    """Number of patch ids gmg_learned_train accepts: the interior vertices
+    of every level, finest level first."""
+    return sum((n_cells // 2 ** l - 1) ** dim for l in range(n_levels))
 
 
 def gmg_learned_corrections(h, level, n_patches, per_patch):

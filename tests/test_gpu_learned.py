@@ -48,7 +48,7 @@ def test_gradients_match_oracle(gmg, dim, k, rank, nh):
 def _train(gmg, P, dim, k, n, steps=300, seed=0):
     import torch
     nint = (2 * k - 1) ** dim
-    npatch = (n - 1) ** dim
+    npatch = gmg.learned_patch_count(dim, n, P.n_levels)
     verts = np.random.default_rng(seed + 1).permutation(npatch)
     res = torch.tensor(np.random.default_rng(seed + 2).standard_normal((npatch, nint)), device="cuda")
     return gmg.gmg_learned_train(P.h, verts, res, steps=steps, batch=min(1024, npatch), lr=3e-3, seed=seed)
@@ -80,12 +80,13 @@ def test_training_reduces_loss_and_sweep_matches_oracle(gmg):
 
 
 def test_learned_correction_gains_over_plain_fd(gmg):
-    """2D Q2 32^2, lognormal coefficient (sigma 1, correlation length 0.1):
+    """2D Q2 32^2, lognormal coefficient (sigma 2, correlation length 0.1;
+    exact local solves need 10 iterations, damped FD 17 in the oracle):
     the corrected local solver needs fewer PCG iterations than plain
     mean-coefficient FD at the same damping."""
     import torch
     dim, k, n, L = 2, 2, 32, 3
-    coef = inputs.lognormal_coefficient(dim, n, 21)
+    coef = inputs.lognormal_coefficient(dim, n, 21, sigma=2.0)
     b = inputs.random_nodal(dim, k, n, 22)
     its = {}
     for mode in ("fd", "learned"):
@@ -98,3 +99,23 @@ def test_learned_correction_gains_over_plain_fd(gmg):
         _, st = gmg.cg_gmg_solve(P.h, u, P.to_device(b, dtype=torch.float64), 1e-10, 200)
         its[mode] = st.iterations
     assert its["learned"] < its["fd"], its
+
+
+def test_sample_ids_span_all_levels(gmg):
+    """Patch ids run over every level, finest first; one past the last is
+    rejected with GMG_ERR_INVALID_ARG before any work."""
+    import torch
+    dim, k, n = 2, 2, 16
+    P = gmg.Problem(dim, k, n, n_levels=3)
+    gmg.gmg_set_coefficient(P.h, inputs.lognormal_coefficient(dim, n, 41))
+    total = gmg.learned_patch_count(dim, n, P.n_levels)
+    assert total == 15 ** 2 + 7 ** 2 + 3 ** 2
+    nint = (2 * k - 1) ** dim
+    res = torch.zeros((1, nint), dtype=torch.float64, device="cuda")
+    with pytest.raises(gmg.GmgError) as e:
+        gmg.gmg_learned_train(P.h, [total], res, steps=1, batch=1)
+    assert e.value.status == -1
+    # the coarsest patches alone are valid training data
+    res = torch.tensor(np.random.default_rng(42).standard_normal((9, nint)), device="cuda")
+    hist, kept = gmg.gmg_learned_train(P.h, np.arange(total - 9, total), res, steps=5, batch=9)
+    assert len(hist) == 5 and all(np.isfinite(hist))

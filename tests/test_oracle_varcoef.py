@@ -82,3 +82,26 @@ def test_learned_gradients_match_finite_differences():
             P[idx] = old
             fd = (lp - lm) / (2 * eps)
             assert abs(fd - G[idx]) <= 1e-7 * max(1.0, abs(fd)), (idx, fd, G[idx])
+
+
+@pytest.mark.parametrize("dim,k", [(2, 2), (3, 2), (3, 3)])
+def test_fd_mean_damped_local_update_is_a_contraction(dim, k):
+    """A_j <= max_c a_c h^{d-2} Ahat_j (cell-wise), so the damped local update
+    B_j A_j with B_j = theta_j/abar h^{2-d} Ahat_j^{-1},
+    theta_j = min(1, 1.8 abar / max a), has its spectrum in (0, 1.8]; the
+    bound is attained up to the spectrum of the coefficient-ratio pencil, so
+    some patch of a strongly varying field overshoots beyond 2 undamped."""
+    n = 6
+    m = Mesh(dim, k, n)
+    coef = inputs.lognormal_coefficient(dim, n, 11, sigma=1.5, corr_len=0.05)
+    sm = VarPatchSmoother(m, coef, "fd_mean")
+    worst_undamped = 0.0
+    for v in m.vertices():
+        Abar, _, abar, theta = sm._patch(v)
+        inner = m.patch_block()[1]
+        Aj = Abar[:, inner]
+        B = sm.local_solve(v, np.eye(Aj.shape[0]))
+        lam = np.linalg.eigvals(B @ Aj).real
+        assert lam.min() > 0 and lam.max() <= 1.8 + 1e-9
+        worst_undamped = max(worst_undamped, lam.max() / theta)
+    assert worst_undamped > 2.0
