@@ -43,12 +43,24 @@ enum gmg_status {
   GMG_ERR_NONFINITE = -4,     /* NaN/Inf met in a solver scalar */
   GMG_ERR_BREAKDOWN = -5,     /* CG breakdown: p^T A p <= 0 or r^T z <= 0 */
   GMG_ERR_NOT_CONVERGED = -6, /* max_it reached above the tolerance */
-  GMG_ERR_UNSUPPORTED = -7    /* valid but not implemented combination */
+  GMG_ERR_UNSUPPORTED = -7,   /* valid but not implemented combination */
+  GMG_ERR_TIMEOUT = -8        /* a bounded device-side wait expired (tensor-core sweep) */
 };
 
 enum gmg_precision {
   GMG_FP64 = 0,  /* smoother, transfer and V-cycle in double */
-  GMG_FP32 = 1   /* smoother, transfer and V-cycle in float (inside FP64 CG) */
+  GMG_FP32 = 1,  /* smoother, transfer and V-cycle in float (inside FP64 CG) */
+  GMG_FP32_TC = 2,  /* as GMG_FP32, and for 3D degrees 4..7 the combined
+                       sweep's 1D contractions run on the tensor cores with
+                       FP32 accumulation, each factor split into its TF32
+                       rounding and the TF32 rounding of the remainder, three
+                       MMAs per product (hi*hi + lo*hi + hi*lo: FP32-level
+                       accuracy); other degrees, 2D and the sweep variants
+                       use the FP32 kernels */
+  GMG_FP32_TF32 = 3 /* as GMG_FP32_TC with data and matrices rounded to TF32
+                       once (one MMA per product; the smoother then depends on
+                       its input's rounding and the outer CG needs more
+                       iterations) */
 };
 
 enum gmg_sweep_variant {
@@ -318,6 +330,24 @@ int gmg_mlp_loss_grad(int dim, int degree, int rank, int hidden, int n, const fl
  * row-major, caller-allocated, of (2k-1)^2 (M, K, T) and 2k-1 (lambda)
  * doubles; any may be NULL. */
 int gmg_patch_fd_1d(int degree, double* M, double* K, double* T, double* lambda);
+
+/* ---- Tensor-core sweep (GMG_FP32_TC) -----------------------------------
+ * Every patch of one colour is processed as in gmg_smooth (Algorithm 4,
+ * local_update of Sec. 3.1: gather, local residual by sum factorisation,
+ * fast-diagonalisation solve of App. A.3, scatter), with each 1D
+ * contraction executed as a TF32 tcgen05 MMA over the lines of the patch
+ * tensor.  Waits on the tensor cores are bounded; an expired wait makes the
+ * kernel return early and set a device flag.
+ * gmg_tc_status synchronises the device, returns GMG_OK or the recorded
+ * status (GMG_ERR_TIMEOUT) and clears it. */
+int gmg_tc_status(void);
+
+/* Diagnostic of the tensor-core encoding: D = A B^T for one 128 x 16 (A) by
+ * 32 x 16 (B) TF32 product on the tensor cores, one MMA tile, as the sweep
+ * kernel issues it.  A, B, D are HOST arrays, row-major (A 128x16, B 32x16,
+ * D 128x32 floats); inputs are rounded to TF32.  Allocates and frees device
+ * memory and synchronises. */
+int gmg_tc_probe(const float* A, const float* B, float* D);
 
 /* Number of CUDA kernels this library has enqueued since it was loaded
  * (host-side counter, all problems and devices).  Host-only. */

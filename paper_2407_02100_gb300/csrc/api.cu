@@ -120,6 +120,9 @@ int launch_colour(gmg_problem* p, const PatchLaunch& pl, void* u, const void* b)
   if (pl.n_patches == 0) return GMG_OK;
   if (p->esize == 8)
     return launch_patch_colour<double>(pl, (double*)u, (const double*)b, (const double*)p->dinv, p->stream);
+  const int pr = p->desc.precision;
+  if ((pr == GMG_FP32_TC || pr == GMG_FP32_TF32) && pl.mode == 0 && tc_supported(pl.g.dim, pl.g.k))
+    return launch_patch_tc(pl, (float*)u, (const float*)b, (const float*)p->dinv, pr == GMG_FP32_TC, p->stream);
   return launch_patch_colour<float>(pl, (float*)u, (const float*)b, (const float*)p->dinv, p->stream);
 }
 
@@ -400,6 +403,7 @@ const char* gmg_status_string(int s) {
     case GMG_ERR_BREAKDOWN: return "CG breakdown";
     case GMG_ERR_NOT_CONVERGED: return "not converged";
     case GMG_ERR_UNSUPPORTED: return "unsupported";
+    case GMG_ERR_TIMEOUT: return "device wait timed out";
     default: return "unknown status";
   }
 }
@@ -430,7 +434,7 @@ int gmg_destroy(gmg_problem* p) {
 int gmg::detail::create_problem(const gmg_desc* d, gmg_problem* p, const CreateOptions& opt) {
   p->desc = *d;
   p->stream = (cudaStream_t)d->stream;
-  p->esize = d->precision == GMG_FP32 ? 4 : 8;
+  p->esize = d->precision == GMG_FP64 ? 8 : 4;
   const int dim = d->dim, k = d->degree;
   // level hierarchy: n_levels given, or halve while even and >= 2
   int L = d->n_levels;
@@ -472,6 +476,8 @@ int gmg::detail::create_problem(const gmg_desc* d, gmg_problem* p, const CreateO
   if (!generalized_eigen_mirror(m, Mi, Ki, Tp, lp)) return GMG_ERR_INVALID_ARG;
   CHECK(upload_patch_tables<double>(k, Mp.data(), Kp.data(), Tp.data(), Mc.data(), Kc.data(), p->stream));
   CHECK(upload_patch_tables<float>(k, Mp.data(), Kp.data(), Tp.data(), Mc.data(), Kc.data(), p->stream));
+  if (d->precision == GMG_FP32_TC || d->precision == GMG_FP32_TF32)
+    CHECK(upload_tc_tables(k, Mp.data(), Kp.data(), Tp.data()));
   const int nint = dim == 3 ? m * m * m : m * m;
   std::vector<double> dinv(nint);
   for (int t = 0; t < nint; ++t) {
@@ -555,7 +561,7 @@ int gmg::detail::check_desc(const gmg_desc* d) {
   if (d->dim != 2 && d->dim != 3) return GMG_ERR_INVALID_ARG;
   if (d->degree < 1 || d->degree > kMaxDegree) return GMG_ERR_INVALID_ARG;
   if (d->n_cells < 2 || d->n_levels < 0 || d->n_levels > 30) return GMG_ERR_INVALID_ARG;
-  if (d->precision != GMG_FP64 && d->precision != GMG_FP32) return GMG_ERR_INVALID_ARG;
+  if (d->precision < GMG_FP64 || d->precision > GMG_FP32_TF32) return GMG_ERR_INVALID_ARG;
   if (!std::isfinite(d->damping) || d->pre_sweeps < 0 || d->post_sweeps < 0) return GMG_ERR_INVALID_ARG;
   // node counts must fit 32-bit lattice indices
   if ((long long)d->n_cells * d->degree + 1 > (1 << 20)) return GMG_ERR_INVALID_ARG;

@@ -92,6 +92,10 @@ int batch_colour(gmg_batch* B, int depth, int colour, bool finest_user, void* u_
     return launch_patch_table<double>(dim, k, pls.data(), (double* const*)us.data(),
                                       (const double* const*)bs.data(), (int)pls.size(),
                                       (const double*)B->probs[0]->dinv, B->ppc, B->stream);
+  const int pr = B->desc.precision;
+  if ((pr == GMG_FP32_TC || pr == GMG_FP32_TF32) && tc_supported(dim, k))
+    return launch_patch_table_tc(dim, k, pls.data(), (float* const*)us.data(), (const float* const*)bs.data(),
+                                 (int)pls.size(), (const float*)B->probs[0]->dinv, pr == GMG_FP32_TC, B->stream);
   return launch_patch_table<float>(dim, k, pls.data(), (float* const*)us.data(),
                                    (const float* const*)bs.data(), (int)pls.size(),
                                    (const float*)B->probs[0]->dinv, B->ppc, B->stream);
@@ -257,7 +261,7 @@ int gmg_batch_create(const gmg_desc* desc, int n_problems, const int* n_cells, g
   if (!B) return GMG_ERR_OOM;
   B->desc = *desc;
   B->stream = (cudaStream_t)desc->stream;
-  B->esize = desc->precision == GMG_FP32 ? 4 : 8;
+  B->esize = desc->precision == GMG_FP64 ? 8 : 4;
   B->n = n_problems;
   // layout of the concatenated finest vectors (each problem 64-element aligned)
   for (int i = 0; i < n_problems; ++i) {

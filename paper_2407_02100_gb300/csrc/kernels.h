@@ -99,6 +99,16 @@ int launch_patch_colour(const PatchLaunch& pl, T* u, const T* b, const T* dinv, 
 template <typename T>
 int launch_patch_table(int dim, int k, const PatchLaunch* pls, T* const* us, const T* const* bs,
                        int n, const T* dinv, int ppc, cudaStream_t s);
+// Tensor-core sweep (patch_tc.cu): 3D, FP32 data, degrees 4..7, combined
+// mode only (GMG_ERR_UNSUPPORTED otherwise).
+bool tc_supported(int dim, int k);
+int upload_tc_tables(int k, const double* Mp, const double* Kp, const double* That);
+// split: data operands as TF32 hi + remainder (GMG_FP32_TC), else TF32 once
+int launch_patch_tc(const PatchLaunch& pl, float* u, const float* b, const float* dinv, bool split,
+                    cudaStream_t s);
+int launch_patch_table_tc(int dim, int k, const PatchLaunch* pls, float* const* us, const float* const* bs,
+                          int n, const float* dinv, bool split, cudaStream_t s);
+
 template <typename T>
 int launch_apply(const ApplyLaunch& al, const T* x, T* y, const T* bvec, cudaStream_t s);
 

@@ -19,9 +19,11 @@ LIB_PATH = os.path.join(HERE, "libgmg.so")
 GMG_OK = 0
 GMG_FP64 = 0
 GMG_FP32 = 1
+GMG_FP32_TC = 2
+GMG_FP32_TF32 = 3
 STATUS = {0: "ok", -1: "invalid argument", -2: "device out of memory", -3: "CUDA error",
           -4: "non-finite value in solver", -5: "CG breakdown", -6: "not converged",
-          -7: "unsupported"}
+          -7: "unsupported", -8: "device wait timed out"}
 
 EXPORTS = ["gmg_create", "gmg_destroy", "gmg_vector_layout", "gmg_level_info",
            "gmg_apply_operator", "gmg_apply_operator_f64", "gmg_smooth", "gmg_smooth_colour",
@@ -31,7 +33,7 @@ EXPORTS = ["gmg_create", "gmg_destroy", "gmg_vector_layout", "gmg_level_info",
            "gmg_batch_layout", "gmg_batch_problem", "gmg_batch_smooth", "gmg_batch_vcycle",
            "gmg_batch_cg_solve", "gmg_batch_autotune", "gmg_batch_set_ppc",
            "gmg_set_coefficient", "gmg_set_local_solver", "gmg_learned_train",
-           "gmg_learned_corrections", "gmg_mlp_loss_grad"]
+           "gmg_learned_corrections", "gmg_mlp_loss_grad", "gmg_tc_status", "gmg_tc_probe"]
 GMG_LOCAL_FD_MEAN, GMG_LOCAL_LEARNED = 0, 1
 GMG_SWEEP_COMBINED, GMG_SWEEP_SEPARATED, GMG_SWEEP_BATCHED = 0, 1, 2
 
@@ -101,6 +103,8 @@ def lib():
             "gmg_mlp_loss_grad": [i, i, i, i, i, vp, vp, vp, vp, vp, ctypes.POINTER(d), vp],
             "gmg_smooth_noalloc": [i, i, i, d, vp, vp, i, i, vp],
             "gmg_status_string": [i],
+            "gmg_tc_status": [],
+            "gmg_tc_probe": [vp, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -271,6 +275,23 @@ def gmg_mlp_loss_grad(dim, degree, rank, hidden, params, X, R, DFD, DEX):
 
 def gmg_kernel_launch_count():
     return lib().gmg_kernel_launch_count()
+
+
+def gmg_tc_status():
+    """Synchronise; the status recorded by the tensor-core sweep (cleared)."""
+    return lib().gmg_tc_status()
+
+
+def gmg_tc_probe(A, B):
+    """D = A B^T on the tensor cores (A 128x16, B 32x16 float32, host)."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    assert A.shape == (128, 16) and B.shape == (32, 16)
+    D = np.zeros((128, 32), dtype=np.float32)
+    _check("gmg_tc_probe", lib().gmg_tc_probe(A.ctypes.data_as(ctypes.c_void_p),
+                                             B.ctypes.data_as(ctypes.c_void_p),
+                                             D.ctypes.data_as(ctypes.c_void_p)))
+    return D
 
 
 def gmg_status_string(status):

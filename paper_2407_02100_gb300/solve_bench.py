@@ -1,5 +1,6 @@
 """GMG-PCG time to solution for one problem, FP64 smoother against the FP32
-smoother / V-cycle inside the same FP64 CG (the outer residual, dot products
+smoother / V-cycle (FFMA kernels, and with the tensor-core TF32 sweep)
+inside the same FP64 CG (the outer residual, dot products
 and coarse data stay FP64), with iteration counts and the difference between
 the two solutions.
 
@@ -28,7 +29,8 @@ def main():
     nodes = (a.n * a.degree + 1) ** a.dim
     out = {"dim": a.dim, "degree": a.degree, "n_cells": a.n, "nodes": nodes, "rtol": a.rtol}
     sols = {}
-    for name, prec in (("fp64", gmg.GMG_FP64), ("fp32_mixed", gmg.GMG_FP32)):
+    for name, prec in (("fp64", gmg.GMG_FP64), ("fp32_mixed", gmg.GMG_FP32), ("fp32_tc_mixed", gmg.GMG_FP32_TC),
+                       ("fp32_tf32_mixed", gmg.GMG_FP32_TF32)):
         P = gmg.Problem(a.dim, a.degree, a.n, precision=prec)
         b = P.to_device(rhs, dtype=torch.float64)
         u = P.zeros(dtype=torch.float64)
@@ -49,9 +51,10 @@ def main():
         out[name] = {"time_to_solution_ms": ms, "mdofs": nodes / ms * 1e3 / 1e6,
                      "iterations": st.iterations, "final_rel_residual": res, "levels": P.n_levels}
         del P
-    out["fp32_mixed"]["rel_diff_vs_fp64_solution"] = float(
-        torch.linalg.vector_norm(sols["fp32_mixed"] - sols["fp64"]) / torch.linalg.vector_norm(sols["fp64"]))
-    out["speedup_fp32_mixed"] = out["fp64"]["time_to_solution_ms"] / out["fp32_mixed"]["time_to_solution_ms"]
+    for name in ("fp32_mixed", "fp32_tc_mixed", "fp32_tf32_mixed"):
+        out[name]["rel_diff_vs_fp64_solution"] = float(
+            torch.linalg.vector_norm(sols[name] - sols["fp64"]) / torch.linalg.vector_norm(sols["fp64"]))
+        out["speedup_" + name] = out["fp64"]["time_to_solution_ms"] / out[name]["time_to_solution_ms"]
     print(json.dumps(out))
 
 

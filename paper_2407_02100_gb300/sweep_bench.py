@@ -22,7 +22,7 @@ def main():
     ap.add_argument("--dim", type=int, default=3)
     ap.add_argument("--degree", type=int, default=4)
     ap.add_argument("--n", type=int, default=64)
-    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "fp32_tc", "fp32_tf32"], default="fp64")
     ap.add_argument("--sweeps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--variant", choices=["combined", "separated", "batched"], default="combined",
@@ -30,7 +30,8 @@ def main():
     ap.add_argument("--batch", type=int, default=32768, help="n_B of Algorithm 5")
     a = ap.parse_args()
     build.build()
-    prec = gmg.GMG_FP64 if a.precision == "fp64" else gmg.GMG_FP32
+    prec = {"fp64": gmg.GMG_FP64, "fp32": gmg.GMG_FP32, "fp32_tc": gmg.GMG_FP32_TC,
+            "fp32_tf32": gmg.GMG_FP32_TF32}[a.precision]
     P = gmg.Problem(a.dim, a.degree, a.n, n_levels=1, precision=prec)
     u = P.to_device(inputs.random_nodal(a.dim, a.degree, a.n, 1))
     b = P.to_device(inputs.random_nodal(a.dim, a.degree, a.n, 2))
