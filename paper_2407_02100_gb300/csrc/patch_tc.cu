@@ -245,16 +245,17 @@ struct TcDims {
   static constexpr int TCOLS = TZ * 32 <= 32 ? 32 : 64;  // TMEM columns (power of two)
   static constexpr int OPB = TZ * kTileB;                  // bytes per operand buffer
   static constexpr int NINT = M * M * M;
-  // operand buffers U, P, Q (and their remainder twins U', P', Q' at +LO)
-  static constexpr int LO = SPLIT ? 3 * OPB : 0;
-  static constexpr int OFF_U = 0, OFF_P = OPB, OFF_Q = 2 * OPB, OFF_B = (SPLIT ? 6 : 3) * OPB;
+  // two operand buffers (and their remainder twins at +LO): the closure U
+  // is dead once stage Z's MMAs are done, so P takes its buffer
+  static constexpr int LO = SPLIT ? 2 * OPB : 0;
+  static constexpr int OFF_U = 0, OFF_P = 0, OFF_Q = OPB, OFF_B = (SPLIT ? 4 : 2) * OPB;
   static constexpr int SMEM = OFF_B + (SPLIT ? 2 : 1) * kBopsFloats * 4;
   static_assert(C <= kKP, "closure must fit the padded contraction length");
   static_assert(TZ <= 2 && TY <= TZ && TX <= TZ, "at most two line tiles per stage");
 };
 
 template <int K, bool SPLIT>
-__global__ void __launch_bounds__(128) patch_tc_kernel(const __grid_constant__ PatchTable tab,
+__global__ void __launch_bounds__(128, K >= 6 ? 3 : 4) patch_tc_kernel(const __grid_constant__ PatchTable tab,
                                                        const float* __restrict__ dinv,
                                                        const float* __restrict__ bops, int* __restrict__ err) {
   using D = TcDims<K, SPLIT>;
@@ -478,7 +479,7 @@ __global__ void __launch_bounds__(128) patch_tc_kernel(const __grid_constant__ P
       }
     }
     stage_sync();
-    // ---- BX and scatter: u_interior += omega d (u_old from the gathered closure) ----
+    // ---- BX and scatter: u_interior += omega d ----
     if (tid == 0) stage_mma(tmem, D::TX, 32, I16, aQ, aB + kBTN, 0, 0, &s_mbar, LO);
     wait_mma();
 #pragma unroll
@@ -491,10 +492,9 @@ __global__ void __launch_bounds__(128) patch_tc_kernel(const __grid_constant__ P
         const long long g = org + 1 + py * (y + 1) + pz * (z + 1);
 #pragma unroll
         for (int i = 0; i < M; ++i) {
-          // the gathered closure holds u exactly unless it was split
-          const float uold = SPLIT ? uo[g + i]
-                                   : *reinterpret_cast<const float*>(OPU + op_off((i + 1) + C * (y + 1), z + 1));
-          uo[g + i] = fmaf(om, v[i], uold);
+          // same-colour patches never write this patch's interior: the
+          // value read is the gathered one
+          uo[g + i] = fmaf(om, v[i], uo[g + i]);
         }
       }
     }
