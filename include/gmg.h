@@ -331,6 +331,28 @@ int gmg_mlp_loss_grad(int dim, int degree, int rank, int hidden, int n, const fl
  * doubles; any may be NULL. */
 int gmg_patch_fd_1d(int degree, double* M, double* K, double* T, double* lambda);
 
+/* ---- Skewed-slab schedule of the sweep (the GPU form of the locality-
+ * ordered batches of Sec. 4.1) ---------------------------------------------
+ * With width W > 0 the patches of a level are grouped into slabs of W
+ * vertex rows along the slowest axis (z in 3D, y in 2D), skewed by the
+ * position o of their colour in the sweep's colour order: patch (v, o) is in
+ * slab floor((v_slow + o) / W).  gmg_smooth (and the V-cycle) then launch one
+ * kernel per (slab, colour) pair, slabs in order, colours in order inside a
+ * slab, so consecutive launches touch about (W + 2) k node planes.  A patch
+ * that overlaps one of an earlier colour position never lands in an earlier
+ * slab, so every patch reads the values Algorithm 4 gives it: results are
+ * bit-identical for every W.  width = 0 restores one launch per colour
+ * (default); width = -1 picks per level the largest W whose node planes of u
+ * and b fit in half of the L2 cache (W >= n - 1 + 2^d is one launch per
+ * colour).  Constant-coefficient problems only (variable-coefficient ones
+ * keep one launch per colour).  Builds the schedules of all levels (device
+ * memory, synchronises). */
+int gmg_set_slab_width(gmg_problem* p, int width);
+
+/* The slab width in effect on `level` (0 = one launch per colour), or a
+ * negative status. */
+int gmg_slab_width(const gmg_problem* p, int level);
+
 /* ---- Tensor-core sweep (GMG_FP32_TC) -----------------------------------
  * Every patch of one colour is processed as in gmg_smooth (Algorithm 4,
  * local_update of Sec. 3.1: gather, local residual by sum factorisation,

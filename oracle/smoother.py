@@ -112,6 +112,22 @@ def colour_sorted_vertices(mesh: Mesh, reverse=False):
     return np.concatenate([mesh.vertices_of_colour(c) for c in order], axis=0)
 
 
+def skewed_slab_sequence(mesh: Mesh, width, reverse=False):
+    """The patch sequence of the skewed-slab schedule (the GPU form of the
+    locality batches of Sec. 4.1; our construction): the patch at vertex v
+    whose colour sits at position o of the colour order (o = c, or
+    n_colours - 1 - c in reverse) belongs to slab (v_slow + o) // width,
+    v_slow its index along the slowest axis; slabs in order, colour
+    positions in order inside a slab, lexicographic within a group."""
+    nc = mesh.n_colours
+    groups = {}
+    for c in range(nc):
+        o = nc - 1 - c if reverse else c
+        for v in mesh.vertices_of_colour(c):
+            groups.setdefault(((int(v[-1]) + o) // width, o), []).append(v)
+    return np.array([v for key in sorted(groups) for v in groups[key]])
+
+
 def morton_key(v):
     """Z-curve (Morton) key of vertex multi-indices v [..., dim]: the bits of
     v_0, v_1 (, v_2) interleaved, v_0 in the lowest position (Sec. 4.1 step 1

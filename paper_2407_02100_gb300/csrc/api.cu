@@ -140,8 +140,91 @@ int smooth_colour(gmg_problem* p, int level, void* u, const void* b, int colour)
   return launch_colour(p, pl, u, b);
 }
 
+// Skewed-slab schedule (the GPU form of the locality-ordered batches of
+// Sec. 4.1): the patch at vertex v of colour c, at position o in the colour
+// order (o = c forward, n_colours - 1 - c in reverse), belongs to slab
+// floor((v_s + o) / W), v_s its vertex index along the slowest axis.  Slabs
+// run in order and colour positions in order inside a slab.  A patch that
+// overlaps a patch of an earlier position (|v - v'|_inf <= 1) never lands in
+// an earlier slab, and patches of one colour do not interact, so every patch
+// reads exactly the values Algorithm 4 gives it: the sweep does not depend
+// on W.  Only the working set between consecutive launches changes: about
+// (W + 2) k node planes of u and b.
+int slab_width_for(const gmg_problem* p, const Level& L) {
+  if (p->varcoef || p->slab_width == 0) return 0;
+  const int nc = 1 << L.g.dim, span = L.g.n - 1 + nc;  // slab index range at W = 1
+  int W = p->slab_width;
+  if (W < 0) {  // the largest slab whose node planes of u and b fill half of the 126 MB L2
+    const long long plane = (L.g.dim == 3 ? L.g.pz : (long long)L.g.py) * (long long)p->esize * 2;
+    W = (int)std::max<long long>(1, (63ll << 20) / std::max<long long>(plane * L.g.k, 1) - 2);
+  }
+  return W >= span ? 0 : W;
+}
+
+int build_slabs(gmg_problem* p, int level, int W) {
+  Level& L = p->levels[level];
+  if (L.slab_w == W) return GMG_OK;
+  for (int d = 0; d < 2; ++d) {
+    if (L.slist[d]) {
+      cudaFree(L.slist[d]);
+      p->owned.erase(std::find(p->owned.begin(), p->owned.end(), (void*)L.slist[d]));
+      L.slist[d] = nullptr;
+    }
+    L.soff[d].clear();
+  }
+  L.slab_w = 0;
+  if (W <= 0) return GMG_OK;
+  const int dim = L.g.dim, nc = 1 << dim, slow = dim - 1;
+  const int nslab = (L.g.n - 1 + nc - 1) / W + 1;
+  for (int d = 0; d < 2; ++d) {
+    std::vector<std::vector<int>> bucket((size_t)nslab * nc);
+    for (int c = 0; c < nc; ++c) {
+      const int o = d == 0 ? c : nc - 1 - c;
+      const PatchLaunch pl = colour_launch(L, c, 1.0);
+      for (int pid = 0; pid < pl.n_patches; ++pid) {
+        int rest = pid, v[3] = {0, 0, 0};
+        for (int a = 0; a < dim; ++a) {
+          v[a] = pl.first[a] + 2 * (rest % pl.count[a]);
+          rest /= pl.count[a];
+        }
+        bucket[(size_t)((v[slow] + o) / W) * nc + o].push_back(pid);
+      }
+    }
+    std::vector<int> flat;
+    L.soff[d].assign(1, 0);
+    for (const auto& bk : bucket) {
+      flat.insert(flat.end(), bk.begin(), bk.end());
+      L.soff[d].push_back((int)flat.size());
+    }
+    void* dptr = nullptr;
+    CHECK(dalloc(p, &dptr, std::max<size_t>(flat.size(), 1) * sizeof(int)));
+    L.slist[d] = static_cast<int*>(dptr);
+    if (!flat.empty() &&
+        cudaMemcpy(dptr, flat.data(), flat.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+      return GMG_ERR_CUDA;
+  }
+  L.slab_w = W;
+  return GMG_OK;
+}
+
 int smooth(gmg_problem* p, int level, void* u, const void* b, int n_sweeps, int reverse) {
-  const int nc = 1 << p->levels[level].g.dim;
+  Level& L = p->levels[level];
+  const int nc = 1 << L.g.dim;
+  if (L.slab_w > 0 && !p->varcoef) {
+    const int d = reverse ? 1 : 0;
+    const int nslab = (int)(L.soff[d].size() - 1) / nc;
+    for (int sw = 0; sw < n_sweeps; ++sw)
+      for (int s = 0; s < nslab; ++s)
+        for (int o = 0; o < nc; ++o) {
+          const int lo = L.soff[d][s * nc + o], cnt = L.soff[d][s * nc + o + 1] - lo;
+          if (cnt == 0) continue;
+          PatchLaunch pl = colour_launch(L, d ? nc - 1 - o : o, p->desc.damping);
+          pl.plist = L.slist[d] + lo;
+          pl.n_patches = cnt;
+          CHECK(launch_colour(p, pl, u, b));
+        }
+    return GMG_OK;
+  }
   for (int s = 0; s < n_sweeps; ++s)
     for (int i = 0; i < nc; ++i) CHECK(smooth_colour(p, level, u, b, reverse ? nc - 1 - i : i));
   return GMG_OK;
@@ -701,6 +784,18 @@ int gmg_set_local_solver(gmg_problem* p, int solver) {
     return GMG_OK;
   }
   return GMG_ERR_INVALID_ARG;
+}
+
+int gmg_set_slab_width(gmg_problem* p, int width) {
+  if (!p || width < -1) return GMG_ERR_INVALID_ARG;
+  p->slab_width = width;
+  for (int l = 0; l < (int)p->levels.size(); ++l) CHECK(build_slabs(p, l, slab_width_for(p, p->levels[l])));
+  return cudaDeviceSynchronize() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+}
+
+int gmg_slab_width(const gmg_problem* p, int level) {
+  if (!valid_level(p, level)) return GMG_ERR_INVALID_ARG;
+  return p->levels[level].slab_w;
 }
 
 int gmg_smooth_variant(gmg_problem* p, int level, void* u, const void* b, int variant,

@@ -22,6 +22,13 @@ struct Level {
   // patches of every colour in Z-curve order (Algorithm 5), built on demand
   int* zlist = nullptr;
   int zoff[9] = {0};
+  // skewed-slab schedule of width slab_w (vertex rows along the slowest
+  // axis), for the forward [0] and reverse [1] colour orders: the patches of
+  // (slab s, order position o) are slist[d][soff[d][s * n_colours + o] ..
+  // soff[d][s * n_colours + o + 1]) (lexicographic ids within the colour)
+  int slab_w = 0;
+  int* slist[2] = {nullptr, nullptr};
+  std::vector<int> soff[2];
 };
 
 // Options of problem creation used by batches: the finest level's u, b, r
@@ -74,6 +81,9 @@ struct gmg_problem {
   double* coarse_inv = nullptr;     // dense inverse of the coarsest interior matrix
   int coarse_n = 0;
   std::vector<void*> owned;
+  // skewed-slab schedule request: 0 whole colours, > 0 slab width in
+  // vertex rows, -1 chosen per level to fit L2 (gmg_set_slab_width)
+  int slab_width = 0;
 };
 
 namespace gmg {

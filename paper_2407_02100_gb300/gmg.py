@@ -33,7 +33,8 @@ EXPORTS = ["gmg_create", "gmg_destroy", "gmg_vector_layout", "gmg_level_info",
            "gmg_batch_layout", "gmg_batch_problem", "gmg_batch_smooth", "gmg_batch_vcycle",
            "gmg_batch_cg_solve", "gmg_batch_autotune", "gmg_batch_set_ppc",
            "gmg_set_coefficient", "gmg_set_local_solver", "gmg_learned_train",
-           "gmg_learned_corrections", "gmg_mlp_loss_grad", "gmg_tc_status", "gmg_tc_probe"]
+           "gmg_learned_corrections", "gmg_mlp_loss_grad", "gmg_tc_status", "gmg_tc_probe",
+           "gmg_set_slab_width", "gmg_slab_width"]
 GMG_LOCAL_FD_MEAN, GMG_LOCAL_LEARNED = 0, 1
 GMG_SWEEP_COMBINED, GMG_SWEEP_SEPARATED, GMG_SWEEP_BATCHED = 0, 1, 2
 
@@ -105,6 +106,8 @@ def lib():
             "gmg_status_string": [i],
             "gmg_tc_status": [],
             "gmg_tc_probe": [vp, vp, vp],
+            "gmg_set_slab_width": [vp, i],
+            "gmg_slab_width": [vp, i],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -275,6 +278,17 @@ def gmg_mlp_loss_grad(dim, degree, rank, hidden, params, X, R, DFD, DEX):
 
 def gmg_kernel_launch_count():
     return lib().gmg_kernel_launch_count()
+
+
+def gmg_set_slab_width(h, width):
+    _check("gmg_set_slab_width", lib().gmg_set_slab_width(h, width))
+
+
+def gmg_slab_width(h, level):
+    w = lib().gmg_slab_width(h, level)
+    if w < 0:
+        raise GmgError("gmg_slab_width", w)
+    return w
 
 
 def gmg_tc_status():

@@ -7,7 +7,8 @@ import pytest
 
 from oracle.mesh import Mesh
 from oracle.smoother import (PatchSmoother, batches_alg5, colour_sorted_vertices,
-                             morton_key, sweep_alg1, sweep_alg2, sweep_alg3, sweep_alg5)
+                             morton_key, skewed_slab_sequence, sweep_alg1, sweep_alg2, sweep_alg3,
+                             sweep_alg5)
 from paper_2407_02100_gb300 import inputs
 
 
@@ -197,3 +198,27 @@ def test_algorithm5_limits(dim, k, n):
     np.testing.assert_allclose(sweep_alg2(s, u0, b, seq), ref1, rtol=0, atol=1e-12 * np.abs(ref1).max())
     # a middle batch size differs from Algorithm 4 (the order matters)
     assert np.abs(sweep_alg5(s, u0, b, 3) - s.sweep(u0, b)).max() > 1e-8
+
+
+@pytest.mark.parametrize("dim,k,n", [(2, 2, 8), (3, 1, 6), (3, 2, 5)])
+@pytest.mark.parametrize("reverse", [False, True])
+def test_skewed_slab_order_reproduces_algorithm4_exactly(dim, k, n, reverse):
+    """Any slab width gives a patch sequence in which every patch reads the
+    values Algorithm 4 gives it: Algorithm 2 in that order equals Algorithm 2
+    in colour order bit for bit (the same per-patch arithmetic on the same
+    inputs), and the batched Algorithm 4 to rounding.  A non-skewed slab
+    order (slab from v alone) does not, which shows the test can fail."""
+    m = Mesh(dim, k, n)
+    s = PatchSmoother(m)
+    u0, b = _rand(m, 61), _rand(m, 62)
+    ref = s.sweep(u0, b, reverse=reverse)
+    ref2 = sweep_alg2(s, u0, b, colour_sorted_vertices(m, reverse))
+    assert np.abs(ref2 - ref).max() <= 1e-12 * np.abs(ref).max()
+    for width in (1, 2, 3, n + 8):
+        seq = skewed_slab_sequence(m, width, reverse)
+        assert sorted(map(tuple, seq)) == sorted(map(tuple, m.vertices()))
+        assert np.array_equal(sweep_alg2(s, u0, b, seq), ref2), width
+    nc = m.n_colours
+    plain = sorted(m.vertices(), key=lambda v: (int(v[-1]), (nc - 1 - int(m.colour(v[None, :])[0]))
+                                                if reverse else int(m.colour(v[None, :])[0])))
+    assert np.abs(sweep_alg2(s, u0, b, np.array(plain)) - ref).max() > 1e-8
