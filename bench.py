@@ -45,6 +45,8 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 # 29,791-patch colour 0, scaled by patches to the 31,256-patch average)
 TRAFFIC_PER_LAUNCH = 282.805760e6 * 31256.0 / 29791.0
 CPU_SAMPLE = dict(dim=3, degree=4, n_cells=8, n_levels=3)
+WORKLOAD = ("3D Poisson Q4, 64^3 cells, FP64 GMG(V(1,1), 8-colour vertex-patch smoother) "
+            "preconditioned CG to 1e-10")
 
 
 def max_over_ranks(value, dist=None, device="cpu"):
@@ -181,8 +183,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(vals) / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded U[-1,1] RHS)",
-        "config": {"workload": "3D Poisson Q4, GMG-PCG to 1e-10 (oracle on bounded sample)",
-                   "sample": cpu_sample_text()},
+        "config": {"workload": WORKLOAD, "sample": cpu_sample_text()},
         "cpu_baseline": {"value": value, "unit": "MDoF/s", "cores": cores, "kind": "oracle",
                          "sample": cpu_sample_text()},
         "e2e": {"value": value, "unit": "MDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -350,8 +351,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic (seeded U[-1,1] RHS on interior nodes)",
-        "config": {"workload": "3D Poisson Q4, 64^3 cells, FP64 GMG(V(1,1), 8-colour vertex-patch "
-                               "smoother) preconditioned CG to 1e-10",
+        "config": {"workload": WORKLOAD,
                    "nodes": nodes, "interior_dofs": (N_CELLS * DEGREE - 1) ** DIM,
                    "levels": P.n_levels, "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "inputs larger than L2 (u, b: 136 MB each)",

@@ -367,9 +367,12 @@ int gmg_tc_status(void);
 /* Diagnostic of the tensor-core encoding: D = A B^T for one 128 x 16 (A) by
  * 32 x 16 (B) TF32 product on the tensor cores, one MMA tile, as the sweep
  * kernel issues it.  A, B, D are HOST arrays, row-major (A 128x16, B 32x16,
- * D 128x32 floats); inputs are rounded to TF32.  Allocates and frees device
- * memory and synchronises. */
-int gmg_tc_probe(const float* A, const float* B, float* D);
+ * D 128x32 floats); inputs are rounded to TF32.  With force_timeout != 0 the
+ * MMA completion is signalled only after a short bounded wait has expired:
+ * the call then returns GMG_ERR_TIMEOUT (the sweep kernel's failure path)
+ * and D still holds the product.  Allocates and frees device memory and
+ * synchronises. */
+int gmg_tc_probe(const float* A, const float* B, float* D, int force_timeout);
 
 /* Number of CUDA kernels this library has enqueued since it was loaded
  * (host-side counter, all problems and devices).  Host-only. */

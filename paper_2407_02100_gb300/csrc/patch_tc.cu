@@ -146,11 +146,11 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* mbar, uint32_t parity) 
 }
 // bounded wait for the phase with the given parity to complete: a
 // non-blocking poll first (the MMAs of a stage finish within a few hundred
-// cycles), then the suspending form
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+// cycles), then at most `limit` suspending tries
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t limit = kWaitLimit) {
   for (int i = 0; i < 4096; ++i)
     if (mbar_test_wait(mbar, parity)) return true;
-  for (uint32_t i = 0; i < kWaitLimit; ++i)
+  for (uint32_t i = 0; i < limit; ++i)
     if (mbar_try_wait(mbar, parity)) return true;
   return false;
 }
@@ -510,9 +510,13 @@ __global__ void __launch_bounds__(128, K >= 6 ? 3 : 4) patch_tc_kernel(const __g
 }
 
 // One 128 x 16 by 16 x 32 TF32 product on the tensor cores (the encoding
-// check of the descriptors used above): D = A B^T.
+// check of the descriptors used above): D = A B^T.  With no_commit the MMAs
+// are issued but their completion is never signalled, so the bounded wait
+// expires and the kernel reports GMG_ERR_TIMEOUT (the failure path of the
+// sweep kernel, exercised without a fault).
 __global__ void __launch_bounds__(128) tc_probe_kernel(const float* __restrict__ A, const float* __restrict__ B,
-                                                       float* __restrict__ Dout, int* __restrict__ err) {
+                                                       float* __restrict__ Dout, int* __restrict__ err,
+                                                       int no_commit) {
   __shared__ __align__(1024) unsigned char sa[kTileB];
   __shared__ __align__(1024) unsigned char sbm[32 * kRowB];
   __shared__ uint64_t s_mbar;
@@ -528,8 +532,21 @@ __global__ void __launch_bounds__(128) tc_probe_kernel(const float* __restrict__
   __syncthreads();
   fence_after();
   const uint32_t tmem = s_tmem;
-  if (tid == 0) stage_mma(tmem, 1, 32, idesc_tf32(128, 32), smem_u32(sa), smem_u32(sbm), 0, 0, &s_mbar);
-  const bool ok = mbar_wait(&s_mbar, 0);
+  if (tid == 0) {
+    if (no_commit) {
+      fence_after();
+      for (int kk = 0; kk < 2; ++kk)
+        mma_tf32(tmem, sdesc(smem_u32(sa) + kk * 2 * kChunkB), sdesc(smem_u32(sbm) + kk * 2 * kChunkB),
+                 idesc_tf32(128, 32), kk);
+    } else {
+      stage_mma(tmem, 1, 32, idesc_tf32(128, 32), smem_u32(sa), smem_u32(sbm), 0, 0, &s_mbar);
+    }
+  }
+  const bool ok = mbar_wait(&s_mbar, 0, no_commit ? 4096u : kWaitLimit);
+  if (no_commit) {  // let the uncommitted MMAs retire before the TMEM is read and freed
+    if (tid == 0) mma_commit(&s_mbar);
+    mbar_wait(&s_mbar, 0);
+  }
   fence_after();
   float v[32];
   tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
@@ -700,7 +717,7 @@ int gmg_tc_status(void) {
   return h == 0 ? GMG_OK : h;
 }
 
-int gmg_tc_probe(const float* A, const float* B, float* Dout) {
+int gmg_tc_probe(const float* A, const float* B, float* Dout, int force_timeout) {
   if (!A || !B || !Dout) return GMG_ERR_INVALID_ARG;
   float *dA = nullptr, *dB = nullptr, *dD = nullptr;
   int* dE = nullptr;
@@ -713,7 +730,7 @@ int gmg_tc_probe(const float* A, const float* B, float* Dout) {
              cudaMemset(dE, 0, 4) != cudaSuccess) {
     st = GMG_ERR_CUDA;
   } else {
-    gmg::tc::tc_probe_kernel<<<1, 128>>>(dA, dB, dD, dE);
+    gmg::tc::tc_probe_kernel<<<1, 128>>>(dA, dB, dD, dE, force_timeout ? 1 : 0);
     gmg::count_launch();
     int e = 0;
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||

@@ -105,7 +105,7 @@ def lib():
             "gmg_smooth_noalloc": [i, i, i, d, vp, vp, i, i, vp],
             "gmg_status_string": [i],
             "gmg_tc_status": [],
-            "gmg_tc_probe": [vp, vp, vp],
+            "gmg_tc_probe": [vp, vp, vp, i],
             "gmg_set_slab_width": [vp, i],
             "gmg_slab_width": [vp, i],
         }
@@ -296,15 +296,18 @@ def gmg_tc_status():
     return lib().gmg_tc_status()
 
 
-def gmg_tc_probe(A, B):
-    """D = A B^T on the tensor cores (A 128x16, B 32x16 float32, host)."""
+def gmg_tc_probe(A, B, force_timeout=False, raise_on_error=True):
+    """D = A B^T on the tensor cores (A 128x16, B 32x16 float32, host).
+    With raise_on_error=False returns (status, D)."""
     A = np.ascontiguousarray(A, dtype=np.float32)
     B = np.ascontiguousarray(B, dtype=np.float32)
     assert A.shape == (128, 16) and B.shape == (32, 16)
     D = np.zeros((128, 32), dtype=np.float32)
-    _check("gmg_tc_probe", lib().gmg_tc_probe(A.ctypes.data_as(ctypes.c_void_p),
-                                             B.ctypes.data_as(ctypes.c_void_p),
-                                             D.ctypes.data_as(ctypes.c_void_p)))
+    st = lib().gmg_tc_probe(A.ctypes.data_as(ctypes.c_void_p), B.ctypes.data_as(ctypes.c_void_p),
+                            D.ctypes.data_as(ctypes.c_void_p), 1 if force_timeout else 0)
+    if not raise_on_error:
+        return st, D
+    _check("gmg_tc_probe", st)
     return D
 
 

@@ -49,6 +49,19 @@ def test_probe_is_exact_on_integers(gmg):
     np.testing.assert_array_equal(D, A @ B.T)
 
 
+def test_expired_wait_is_reported_as_a_status(gmg):
+    """The MMA completion is withheld until a short bounded wait has run out:
+    the kernel returns GMG_ERR_TIMEOUT instead of hanging or trapping, the
+    context stays usable and the next call succeeds."""
+    rng = np.random.default_rng(8)
+    A = rng.integers(-8, 9, (128, 16)).astype(np.float32)
+    B = rng.integers(-8, 9, (32, 16)).astype(np.float32)
+    st, D = gmg.gmg_tc_probe(A, B, force_timeout=True, raise_on_error=False)
+    assert st == -8
+    np.testing.assert_array_equal(D, A @ B.T)
+    np.testing.assert_array_equal(gmg.gmg_tc_probe(A, B), A @ B.T)
+
+
 @pytest.mark.parametrize("mode", list(MODES))
 @pytest.mark.parametrize("k,n", [(4, 4), (4, 5), (5, 3), (6, 3), (7, 3)])
 @pytest.mark.parametrize("reverse", [False, True])
