@@ -353,15 +353,18 @@ int gmg_set_slab_width(gmg_problem* p, int width);
  * negative status. */
 int gmg_slab_width(const gmg_problem* p, int level);
 
-/* ---- Tensor-core sweep (GMG_FP32_TC) -----------------------------------
+/* ---- Tensor-core sweep (GMG_FP32_TC) and bounded device waits ----------
  * Every patch of one colour is processed as in gmg_smooth (Algorithm 4,
  * local_update of Sec. 3.1: gather, local residual by sum factorisation,
  * fast-diagonalisation solve of App. A.3, scatter), with each 1D
  * contraction executed as a TF32 tcgen05 MMA over the lines of the patch
- * tensor.  Waits on the tensor cores are bounded; an expired wait makes the
- * kernel return early and set a device flag.
- * gmg_tc_status synchronises the device, returns GMG_OK or the recorded
- * status (GMG_ERR_TIMEOUT) and clears it. */
+ * tensor.  Device-side waits are bounded: on the tensor cores' completion,
+ * and on the TMA gathers of the sweep kernels (every sweep gathers a patch's
+ * closure with one TMA box per vector when the vectors' base addresses are
+ * 16-byte aligned and their pitches multiples of 16 bytes, else with one
+ * cp.async per element).  An expired wait makes the kernel finish early and
+ * set a device flag.  gmg_tc_status synchronises the device, returns GMG_OK
+ * or the recorded status (GMG_ERR_TIMEOUT) and clears it. */
 int gmg_tc_status(void);
 
 /* Diagnostic of the tensor-core encoding: D = A B^T for one 128 x 16 (A) by

@@ -518,6 +518,7 @@ int gmg::detail::create_problem(const gmg_desc* d, gmg_problem* p, const CreateO
   p->desc = *d;
   p->stream = (cudaStream_t)d->stream;
   p->esize = d->precision == GMG_FP64 ? 8 : 4;
+  if (!device_wait_flag()) return GMG_ERR_CUDA;  // resolved once, outside any graph capture
   const int dim = d->dim, k = d->degree;
   // level hierarchy: n_levels given, or halve while even and >= 2
   int L = d->n_levels;

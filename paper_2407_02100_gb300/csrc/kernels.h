@@ -41,6 +41,7 @@ struct PatchLaunch {
 constexpr int kMaxTable = 64;
 struct PatchEntry {
   long long py, pz;     // pitches of the level vectors
+  int N;                // nodes per direction
   int first[3], count[3];
   int n_patches;
   int group_begin;
@@ -82,6 +83,11 @@ struct AxisOp {
   int shift;
   int accumulate;
 };
+
+// Device flag of the bounded device-side waits (TMA gathers, tensor-core
+// MMA completion): set to GMG_ERR_TIMEOUT by a kernel whose wait expired;
+// read and cleared by gmg_tc_status.
+int* device_wait_flag();
 
 // Host-side count of kernel launches made by this library (all launchers
 // call count_launch once per kernel they enqueue).

@@ -17,8 +17,11 @@
 //             (fast diagonalisation, App. A.3)
 //   scatter   u_interior += omega d  (same-colour interiors are disjoint)
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "../../include/gmg.h"
+#include "async.cuh"
 #include "kernels.h"
 
 #ifndef GMG_T
@@ -145,48 +148,91 @@ template <int N>
 __device__ __forceinline__ void async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 // Shared-memory plan of the sweep kernel, per patch (elements):
-//   IN  (NBUF copies): closure of u (C^d), then interior of b (M^d)
+//   IN  (NBUF copies): closure of u, then interior of b, rows of XU / XB
+//       elements ([z][y][x]); with the TMA gather (TMA = true) a row is the
+//       TMA box width: C (resp. M + 1) plus the alignment shift, rounded up to
+//       16 bytes, and each box starts on 128 bytes
 //   WA  3D: stage-y results A1, A2;  2D: stage-y results P, Q
 //   WB  3D: stage-z results P, Q, then r and the FD work;  2D: r and FD work
 // Stage x always reads WA and writes WB.
-template <int DIM, int K>
+template <int DIM, int K, bool TMA = false>
 struct SweepSmem {
   static constexpr int C = 2 * K + 1, M = 2 * K - 1;
-  static constexpr int NCLO = DIM == 3 ? C * C * C : C * C;
+  static constexpr int A = 16 / (int)sizeof(T);  // elements per 16 bytes
+  static constexpr int XU = TMA ? (C + A - 1 + A - 1) / A * A : C;
+  static constexpr int XB = TMA ? XU : M;
+  static constexpr int R128 = 128 / (int)sizeof(T);
+  static constexpr int rnd(int n) { return TMA ? (n + R128 - 1) / R128 * R128 : n; }
+  static constexpr int NCLO = rnd(DIM == 3 ? C * C * XU : C * XU);
+  static constexpr int NBIN = rnd(DIM == 3 ? M * M * XB : M * XB);
   static constexpr int NINT = DIM == 3 ? M * M * M : M * M;
-  static constexpr int IN = NCLO + NINT;
+  static constexpr int IN = NCLO + NBIN;
   static constexpr int WA = DIM == 3 ? 2 * C * M * M : 2 * C * M;
   static constexpr int WB = DIM == 3 ? cmax(2 * C * C * M, M * M * M) : M * M;
   static constexpr int per_patch(int nbuf) { return nbuf * IN + WA + WB; }
+  // TMA box bytes of the closure of u and of the interior rows of b
+  static constexpr int BOX_U = (DIM == 3 ? C * C * XU : C * XU) * (int)sizeof(T);
+  static constexpr int BOX_B = (DIM == 3 ? M * M * XB : M * XB) * (int)sizeof(T);
 };
+
+// Tensor maps of the u and b vectors of each table entry (TMA gather).
+template <int ME>
+struct TmaMaps {
+  CUtensorMap u[ME], b[ME];
+};
+template <>
+struct TmaMaps<0> {};
 
 // One colour of the sweep.  Persistent CTAs walk groups of PPC consecutive
 // patches of the colour.  With NBUF = 2, while a group is computed the next
-// group's closure of u and interior of b stream into the other input buffer
-// (cp.async), so global-memory latency overlaps the contractions; NBUF = 1 is
-// used when two buffers do not fit in shared memory.  Stages (3D; 2D drops
-// the z stages):
+// group's closure of u and interior of b stream into the other input buffer,
+// so global-memory latency overlaps the contractions; NBUF = 1 is used when
+// two buffers do not fit in shared memory.  The gather is either one TMA box
+// per patch and vector (ME > 0: tiled cp.async.bulk.tensor loads issued by one
+// thread, completing on the buffer's mbarrier; the box starts at the closure
+// origin rounded down to 16 bytes and the shift is kept per patch) or one
+// cp.async per element (ME = 0).  Stages (3D; 2D drops the z stages):
 //   z: P,Q | y: A1,A2 | x: r + forward FD along x | forward FD y |
 //   forward FD z, times the FD diagonal | backward FD z | backward FD y |
 //   backward FD x + scatter (u_new = u_old + omega d, u_old from the buffer)
 // Same-colour patches never write each other's closure, so the buffered
 // closure values are the values the gather (eq. "gather") reads.
-template <int DIM, int K, int NT, int PPC, int NBUF>
+template <int DIM, int K, int NT, int PPC, int NBUF, int ME>
 __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant__ PatchTable tab,
-                                                          const T* __restrict__ dinv) {
-  using Z = SweepSmem<DIM, K>;
-  constexpr int C = Z::C, M = Z::M;
+                                                          const T* __restrict__ dinv,
+                                                          const __grid_constant__ TmaMaps<ME> maps,
+                                                          int* __restrict__ err) {
+  constexpr bool TMA = ME > 0;
+  using Z = SweepSmem<DIM, K, TMA>;
+  constexpr int C = Z::C, M = Z::M, XU = Z::XU, XB = Z::XB;
   constexpr int LINES = DIM == 3 ? M * M : M;  // interior lines per axis
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* const IN0 = reinterpret_cast<T*>(smem_raw);       // [NBUF][PPC][IN]
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // TMA boxes start on 128 bytes: the launch adds 128 bytes of slack
+  T* const IN0 = reinterpret_cast<T*>(TMA ? smem_raw + ((128 - (async::smem_u32(smem_raw) & 127)) & 127)
+                                          : smem_raw);  // [NBUF][PPC][IN]
   T* const WA = IN0 + NBUF * PPC * Z::IN;              // [PPC][WA]
   T* const WB = WA + PPC * Z::WA;                      // [PPC][WB]
   __shared__ long long s_origin[2][PPC];
+  __shared__ int s_coord[2][PPC][3];   // closure origin (lattice coordinates), TMA gather
   __shared__ int s_nvalid[2];
   __shared__ int s_entry[2];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  uint32_t phase = 0;  // bit s: parity of the next phase of s_bar[s]
+  bool wait_ok = true;
   const T om = (T)tab.omega;
   const int mode = tab.mode;
   const int ngroups = tab.total_groups;
+  if (TMA && threadIdx.x == 0) {
+    async::mbar_init(&s_bar[0], 1);
+    async::mbar_init(&s_bar[1], 1);
+  }
+  if (TMA) __syncthreads();
+  // element offsets inside a patch's buffers: closure of u at (x, y, z)
+  // (closure coordinates), interior of b at (x, y, z) (interior coordinates)
+  auto uo = [](int x, int y, int z) { return DIM == 3 ? (z * C + y) * XU + x : y * XU + x; };
+  auto bo = [](int x, int y, int z) { return DIM == 3 ? (z * M + y) * XB + x : y * XB + x; };
+  // shift of the patch's closure inside its TMA box (0 without TMA)
+  auto ushift = [&](int slot, int q) { return TMA ? s_coord[slot][q][0] % Z::A : 0; };
 
   // table entry and patch origins of a group (threads 0..PPC-1); callers
   // follow with a barrier
@@ -215,12 +261,35 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
       const long long o1 = (long long)(e.first[1] + 2 * i1 - 1) * K;
       const long long o2 = DIM == 3 ? (long long)(e.first[2] + 2 * i2 - 1) * K : 0;
       s_origin[slot][threadIdx.x] = o0 + e.py * o1 + e.pz * o2;
+      s_coord[slot][threadIdx.x][0] = (int)o0;
+      s_coord[slot][threadIdx.x][1] = (int)o1;
+      s_coord[slot][threadIdx.x][2] = (int)o2;
     }
   };
   // issue the copies of the group whose origins are in `slot` into input
   // buffer `slot`, then commit them as one group
   auto prefetch = [&](int slot) {
     const int nv = s_nvalid[slot];
+    if constexpr (TMA) {
+      if (threadIdx.x == 0) {
+        const int ent = s_entry[slot];
+        T* dst0 = IN0 + slot * PPC * Z::IN;
+        async::mbar_arrive_expect_tx(&s_bar[slot], (uint32_t)(nv * ((mode == 0 ? Z::BOX_U : 0) + Z::BOX_B)));
+        for (int q = 0; q < nv; ++q) {
+          const int x0 = s_coord[slot][q][0], xa = x0 - x0 % Z::A;
+          const int y0 = s_coord[slot][q][1], z0 = s_coord[slot][q][2];
+          T* dst = dst0 + q * Z::IN;
+          if (DIM == 3) {
+            if (mode == 0) async::tma_load_3d(dst, &maps.u[ent], xa, y0, z0, &s_bar[slot]);
+            async::tma_load_3d(dst + Z::NCLO, &maps.b[ent], xa, y0 + 1, z0 + 1, &s_bar[slot]);
+          } else {
+            if (mode == 0) async::tma_load_2d(dst, &maps.u[ent], xa, y0, &s_bar[slot]);
+            async::tma_load_2d(dst + Z::NCLO, &maps.b[ent], xa, y0 + 1, &s_bar[slot]);
+          }
+        }
+      }
+      return;
+    }
     const PatchEntry& e = tab.e[s_entry[slot]];
     const T* __restrict__ u = static_cast<const T*>(e.u);
     const T* __restrict__ b = static_cast<const T*>(e.b);
@@ -243,6 +312,18 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
     async_commit();
   };
 
+  // wait for the gather of `slot`: the TMA phase (bounded; an expired wait
+  // is recorded and the kernel carries on, so it always terminates) or this
+  // thread's cp.async groups (all but `pending` newest)
+  auto wait_gather = [&](int slot, int pending) {
+    if constexpr (TMA) {
+      if (wait_ok && !async::mbar_wait(&s_bar[slot], (phase >> slot) & 1u)) wait_ok = false;
+      phase ^= 1u << slot;
+    } else {
+      if (pending) async_wait<1>();
+      else async_wait<0>();
+    }
+  };
   int grp = blockIdx.x;
   if (NBUF == 2 && grp < ngroups) {
     set_origins(grp, 0);
@@ -255,14 +336,14 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
       set_origins(grp, 0);
       __syncthreads();
       prefetch(0);
-      async_wait<0>();
+      wait_gather(0, 0);
     } else if (grp + (int)gridDim.x < ngroups) {
       set_origins(grp + gridDim.x, cur ^ 1);
       __syncthreads();
       prefetch(cur ^ 1);
-      async_wait<1>();  // this thread's copies of the current group are done
+      wait_gather(cur, 1);  // the current group's copies are done
     } else {
-      async_wait<0>();
+      wait_gather(cur, 0);
     }
     __syncthreads();  // ... and everybody's
     const int nvalid = s_nvalid[cur];
@@ -278,11 +359,11 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
       // ---- stage z: P = Mp_z u, Q = Kp_z u   (dims x:C, y:C, z:M, in WB) ----
       for (int idx = threadIdx.x; idx < nvalid * C * C; idx += NT) {
         const int q = idx / (C * C), l = idx % (C * C);
-        const T* U = IN + q * Z::IN;
+        const T* U = IN + q * Z::IN + ushift(cur, q) + uo(l % C, l / C, 0);
         T* B = WB + q * Z::WB;
         T x[C];
 #pragma unroll
-        for (int j = 0; j < C; ++j) x[j] = U[l + j * C * C];
+        for (int j = 0; j < C; ++j) x[j] = U[j * C * XU];
 #pragma unroll
         for (int i = 0; i < M; ++i) {
           B[l + i * C * C] = patch_row<K, 0>(i, x);
@@ -313,11 +394,11 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
       // ---- stage y: P = Mp_y u, Q = Kp_y u   (dims x:C, y:M, in WA) ----
       for (int idx = threadIdx.x; idx < nvalid * C; idx += NT) {
         const int q = idx / C, l = idx % C;
-        const T* U = IN + q * Z::IN;
+        const T* U = IN + q * Z::IN + ushift(cur, q) + l;
         T* A = WA + q * Z::WA;
         T x[C];
 #pragma unroll
-        for (int j = 0; j < C; ++j) x[j] = U[l + j * C];
+        for (int j = 0; j < C; ++j) x[j] = U[j * XU];
 #pragma unroll
         for (int i = 0; i < M; ++i) {
           A[l + i * C] = patch_row<K, 0>(i, x);
@@ -334,7 +415,9 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
       const int q = idx / LINES, l = idx % LINES;
       constexpr int PLANE = DIM == 3 ? C * M * M : C * M;
       const T* X = WA + q * Z::WA;
-      const T* Bq = IN + q * Z::IN + Z::NCLO;
+      // interior row l of b: x = 0..M-1 at (y, z) = (l % M, l / M) (3D) or y = l (2D)
+      const T* Bq = IN + q * Z::IN + Z::NCLO + (TMA ? ushift(cur, q) + 1 : 0) +
+                    (DIM == 3 ? bo(0, l % M, l / M) : bo(0, l, 0));
       T r[M], y[M];
       if (mode == 0) {
         T a1[C], a2[C];
@@ -345,13 +428,13 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
         }
 #pragma unroll
         for (int i = 0; i < M; ++i) {
-          T acc = sb * Bq[M * l + i];
+          T acc = sb * Bq[i];
           acc = patch_row<K, 1, true>(i, a1, acc);
           r[i] = patch_row<K, 0, true>(i, a2, acc);
         }
       } else {
 #pragma unroll
-        for (int i = 0; i < M; ++i) r[i] = sb * Bq[M * l + i];
+        for (int i = 0; i < M; ++i) r[i] = sb * Bq[i];
       }
       fd_forward<K>(r, y);
       T* R = WB + q * Z::WB + M * l;
@@ -399,9 +482,9 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
     for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {
       const int q = idx / LINES, l = idx % LINES;
       const T* R = WB + q * Z::WB + M * l;
-      const T* U = IN + q * Z::IN;
       // interior line l of the patch: closure row (y+1, z+1), x = 1..M
-      const int cl = DIM == 3 ? (l % M + 1) * C + (l / M + 1) * C * C : (l + 1) * C;
+      const T* U = IN + q * Z::IN + ushift(cur, q) +
+                   (DIM == 3 ? uo(1, l % M + 1, l / M + 1) : uo(1, l + 1, 0));
       T yv[M], d[M];
 #pragma unroll
       for (int i = 0; i < M; ++i) yv[i] = R[i];
@@ -409,10 +492,12 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
       const long long row = s_origin[cur][q] + 1 + py * (l % M + 1) + (DIM == 3 ? pz * (l / M + 1) : 0);
 #pragma unroll
       for (int i = 0; i < M; ++i)
-        u[row + i] = fma(om, d[i], mode == 0 ? U[cl + 1 + i] : u[row + i]);
+        u[row + i] = fma(om, d[i], mode == 0 ? U[i] : u[row + i]);
     }
+    if (TMA) async::fence_proxy_async();  // reads of the buffers before the next TMA writes
     __syncthreads();  // buffers and origins are refilled / reused next iteration
   }
+  if (TMA && !wait_ok) atomicExch(err, GMG_ERR_TIMEOUT);
 }
 
 // ---------------------------------------------------------------------------
@@ -453,7 +538,7 @@ __global__ void __launch_bounds__(NT) apply_kernel(const T* __restrict__ xin, T*
                                                    const T* __restrict__ bvec, ApplyLaunch al) {
   using D = ApplyDims<DIM, K, BC>;
   constexpr int EI = D::EI, EO = D::EO;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);
   T* B = A + D::SA;
   const int N = al.g.N, n = al.g.n;

@@ -1,6 +1,9 @@
 // Launchers for one scalar type; included after patch_kernels.cuh by
 // patch_f64.cu / patch_f32.cu.
 #pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -67,11 +70,57 @@ static inline int table_groups(PatchTable& tab, int ppc) {
   return g;
 }
 
-template <int DIM, int K, int PPC, int NT, int NBUF>
+// ---- TMA gather: tensor maps of the level vectors ----
+static PFN_cuTensorMapEncodeTiled_v12000 tma_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// A vector can be read by the TMA boxes when its base is 16-byte aligned and
+// its row and plane pitches are multiples of 16 bytes.
+static bool tma_usable(const PatchTable& tab, int dim) {
+  if (!tma_encoder()) return false;
+  for (int i = 0; i < tab.n; ++i) {
+    const PatchEntry& e = tab.e[i];
+    if (((uintptr_t)e.u | (uintptr_t)e.b) & 15) return false;
+    if ((e.py * (long long)sizeof(T)) % 16 || (dim == 3 && (e.pz * (long long)sizeof(T)) % 16)) return false;
+    if (e.N < 2) return false;
+  }
+  return true;
+}
+
+// box {XU, rows, rows[, rows]} over the lattice {N, N[, N]} of one vector
+static bool tma_encode(CUtensorMap* m, const void* ptr, int dim, int N, long long py, long long pz, int xbox,
+                       int rows) {
+  const cuuint64_t gdim[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)N};
+  const cuuint64_t gstride[2] = {(cuuint64_t)(py * (long long)sizeof(T)), (cuuint64_t)(pz * (long long)sizeof(T))};
+  const cuuint32_t box[3] = {(cuuint32_t)xbox, (cuuint32_t)rows, (cuuint32_t)rows};
+  const cuuint32_t estride[3] = {1, 1, 1};
+  const CUresult r = tma_encoder()(m, sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                                   (cuuint32_t)dim, const_cast<void*>(ptr), gdim, gstride, box, estride,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int DIM, int K, int PPC, int NT, int NBUF, int ME>
 static int launch_table_cfg(PatchTable& tab, const T* dinv, cudaStream_t s) {
-  constexpr int SMEM = PPC * SweepSmem<DIM, K>::per_patch(NBUF) * (int)sizeof(T);
+  using Z = SweepSmem<DIM, K, (ME > 0)>;
+  constexpr int SMEM = PPC * Z::per_patch(NBUF) * (int)sizeof(T) + (ME > 0 ? 128 : 0);
   static_assert(SMEM <= 227 * 1024, "sweep kernel shared memory exceeds the per-CTA limit");
-  auto kern = patch_colour_kernel<DIM, K, NT, PPC, NBUF>;
+  auto kern = patch_colour_kernel<DIM, K, NT, PPC, NBUF, ME>;
   static int per_sm = 0;  // resident CTAs per SM (persistent grid)
   if (per_sm == 0) {
     if (prepare(kern, SMEM) != GMG_OK) return GMG_ERR_CUDA;
@@ -81,10 +130,32 @@ static int launch_table_cfg(PatchTable& tab, const T* dinv, cudaStream_t s) {
   }
   const int ngroups = table_groups(tab, PPC);
   if (ngroups <= 0) return GMG_OK;
+  TmaMaps<ME> maps;
+  if constexpr (ME > 0) {
+    for (int i = 0; i < tab.n; ++i) {
+      const PatchEntry& e = tab.e[i];
+      if (!tma_encode(&maps.u[i], e.u, DIM, e.N, e.py, e.pz, Z::XU, Z::C) ||
+          !tma_encode(&maps.b[i], e.b, DIM, e.N, e.py, e.pz, Z::XB, Z::M))
+        return GMG_ERR_CUDA;
+    }
+  }
+  int* const flag = device_wait_flag();
+  if (!flag) return GMG_ERR_CUDA;
   const int grid = std::min(ngroups, per_sm * sm_count());
-  kern<<<grid, NT, SMEM, s>>>(tab, dinv);
+  kern<<<grid, NT, SMEM, s>>>(tab, dinv, maps, flag);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+}
+
+// the TMA-gather variant when every vector of the table allows it, else the
+// per-element cp.async gather
+template <int DIM, int K, int PPC, int NT, int NBUF>
+static int launch_table_gather(PatchTable& tab, const T* dinv, cudaStream_t s) {
+  if (tma_usable(tab, DIM)) {
+    if (tab.n == 1) return launch_table_cfg<DIM, K, PPC, NT, NBUF, 1>(tab, dinv, s);
+    return launch_table_cfg<DIM, K, PPC, NT, NBUF, kMaxTable>(tab, dinv, s);
+  }
+  return launch_table_cfg<DIM, K, PPC, NT, NBUF, 0>(tab, dinv, s);
 }
 
 // default configuration (SweepCfg), or a tuned patches-per-CTA variant
@@ -93,14 +164,15 @@ static int launch_table(PatchTable& tab, const T* dinv, int ppc, cudaStream_t s)
   using Cfg = SweepCfg<DIM, K>;
   if constexpr (DIM == 3 && sizeof(T) == 4 && K <= 4) {
     constexpr int NB = SweepCfg<DIM, K>::NBUF;
-    if (ppc == 1) return launch_table_cfg<DIM, K, 1, 128, NB>(tab, dinv, s);
-    if (ppc == 2) return launch_table_cfg<DIM, K, 2, 128, NB>(tab, dinv, s);
-    if (ppc == 4) return launch_table_cfg<DIM, K, 4, 128, NB>(tab, dinv, s);
+    if (ppc == 1) return launch_table_gather<DIM, K, 1, 128, NB>(tab, dinv, s);
+    if (ppc == 2) return launch_table_gather<DIM, K, 2, 128, NB>(tab, dinv, s);
+    if (ppc == 4) return launch_table_gather<DIM, K, 4, 128, NB>(tab, dinv, s);
   }
-  return launch_table_cfg<DIM, K, Cfg::PPC, Cfg::NT, Cfg::NBUF>(tab, dinv, s);
+  return launch_table_gather<DIM, K, Cfg::PPC, Cfg::NT, Cfg::NBUF>(tab, dinv, s);
 }
 
 static void fill_entry(PatchEntry& e, const PatchLaunch& pl, void* u, const void* b) {
+  e.N = pl.g.N;
   e.py = pl.g.py;
   e.pz = pl.g.pz;
   for (int a = 0; a < 3; ++a) {

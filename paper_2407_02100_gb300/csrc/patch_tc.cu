@@ -41,10 +41,17 @@
 #include <vector>
 
 #include "../../include/gmg.h"
+#include "async.cuh"
 #include "kernels.h"
 
 namespace gmg {
 namespace tc {
+
+using async::fence_proxy_async;
+using async::kWaitLimit;
+using async::mbar_init;
+using async::mbar_wait;
+using async::smem_u32;
 
 constexpr int kKP = 16;                // padded contraction length (TF32: 2 MMA K-steps of 8)
 constexpr int kRowB = kKP * 4;         // bytes per operand line
@@ -61,7 +68,6 @@ constexpr int kBKP = 4096;   // Kp         N = 16
 constexpr int kBMP = 5120;   // Mp         N = 16
 constexpr int kBTT = 6144;   // T^T (rows = modes, K = nodes)   N = 16
 constexpr int kBTN = 7168;   // T   (rows = nodes, K = modes)   N = 16
-constexpr uint32_t kWaitLimit = 1u << 20;
 
 // per degree: the B operands rounded to TF32, then the TF32 roundings of the
 // remainders (used by the split form)
@@ -75,10 +81,6 @@ __host__ __device__ constexpr uint32_t op_off(int r, int k) {
 // instruction descriptor: D = F32, A = B = TF32, both K-major, M x N
 __host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
 }
 
 // shared-memory matrix descriptor, K-major, no swizzle
@@ -102,11 +104,6 @@ __device__ __forceinline__ void fence_before() {
 __device__ __forceinline__ void fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 }
-// make this thread's generic-proxy shared-memory writes visible to the
-// tensor core (async proxy)
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
 __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
   asm volatile(
@@ -119,40 +116,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                    smem_u32(mbar))
                : "memory");
-}
-__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      "selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(mbar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_test_wait(uint64_t* mbar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      "selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(mbar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait for the phase with the given parity to complete: a
-// non-blocking poll first (the MMAs of a stage finish within a few hundred
-// cycles), then at most `limit` suspending tries
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t limit = kWaitLimit) {
-  for (int i = 0; i < 4096; ++i)
-    if (mbar_test_wait(mbar, parity)) return true;
-  for (uint32_t i = 0; i < limit; ++i)
-    if (mbar_try_wait(mbar, parity)) return true;
-  return false;
 }
 __device__ __forceinline__ float tf32(float x) {
   uint32_t r;
@@ -626,6 +589,7 @@ int launch_table(int k, bool split, PatchTable& tab, const float* dinv, cudaStre
 }
 
 void fill(PatchEntry& e, const PatchLaunch& pl, void* u, const void* b) {
+  e.N = pl.g.N;
   e.py = pl.g.py;
   e.pz = pl.g.pz;
   for (int a = 0; a < 3; ++a) {
@@ -641,6 +605,15 @@ void fill(PatchEntry& e, const PatchLaunch& pl, void* u, const void* b) {
 }
 
 }  // namespace tc
+
+int* device_wait_flag() {
+  static int* flag = nullptr;
+  if (!flag) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, tc::g_tc_error) == cudaSuccess) flag = static_cast<int*>(p);
+  }
+  return flag;
+}
 
 bool tc_supported(int dim, int k) { return dim == 3 && k >= tc::kMinK && k <= tc::kMaxK; }
 

@@ -156,3 +156,27 @@ def test_pcg(gmg, dim, k, n, L):
     assert abs(st.iterations - its) <= 1, (st.iterations, its)
     got = P.from_device(u)
     assert np.linalg.norm(got - xo) <= 1e-8 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("dim,k,n,prec", [(3, 4, 5, 0), (3, 3, 6, 1), (2, 3, 9, 1), (3, 2, 7, 0)])
+def test_tma_and_elementwise_gathers_agree(gmg, dim, k, n, prec):
+    """Vectors whose base is not 16-byte aligned cannot be read by TMA boxes:
+    the sweep then gathers element by element.  Both gathers feed the same
+    arithmetic, so the results must be bit-identical, and equal to the
+    oracle's sweep to the precision's bound."""
+    import torch
+    P = gmg.Problem(dim, k, n, n_levels=1, precision=prec)
+    u0 = inputs.random_nodal(dim, k, n, 5001)
+    b = inputs.random_nodal(dim, k, n, 5002)
+    ua = P.to_device(u0)
+    bd = P.to_device(b)
+    gmg.gmg_smooth(P.h, 0, ua, bd, 1, False)
+    buf = torch.zeros(ua.numel() + 1, dtype=ua.dtype, device=ua.device)
+    um = buf[1:]                                  # 4 or 8 bytes off 16-byte alignment
+    um.copy_(P.to_device(u0))
+    gmg.gmg_smooth(P.h, 0, um, bd, 1, False)
+    assert gmg.gmg_tc_status() == 0
+    assert torch.equal(ua, um)
+    ref = PatchSmoother(Mesh(dim, k, n)).sweep(u0, b)
+    got = P.from_device(ua)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < (1e-12 if prec == 0 else 1e-5)
