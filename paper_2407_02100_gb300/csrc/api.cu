@@ -411,13 +411,13 @@ int restrict_to(gmg_problem* p, int fl, const void* fine, void* coarse) {
   return GMG_OK;
 }
 
-int coarse_solve(gmg_problem* p, const void* b, void* x) {
+// Exact coarsest-level solve of the constant-coefficient problem by global
+// fast diagonalisation (App. A.3 applied to the whole level): x = (T..T)
+// diag(h^{2-d} / sum lambda) (T..T)^T b on the interior, in element type E.
+template <typename E>
+int coarse_fd(gmg_problem* p, const void* b, void* x, const void* fwd, const void* bwd, const void* dinv,
+              void* t1, void* t2) {
   const LevelGeom& g = p->levels[0].g;
-  if (p->varcoef) {
-    if (p->esize == 8)
-      return launch_dense_solve<double>(g, p->coarse_inv, p->coarse_n, (const double*)b, (double*)x, p->stream);
-    return launch_dense_solve<float>(g, p->coarse_inv, p->coarse_n, (const float*)b, (float*)x, p->stream);
-  }
   const int dim = g.dim, m = p->m0;
   const int zero[3] = {0, 0, 0};
   const int one[3] = {1, 1, dim == 3 ? 1 : 0};
@@ -429,28 +429,43 @@ int coarse_solve(gmg_problem* p, const void* b, void* x) {
   Arr cur = lev;
   for (int a = 0; a < dim; ++a) {
     const bool first = (a == 0);
-    void* dst = (a % 2 == 0) ? p->ctmp1 : p->ctmp2;
+    void* dst = (a % 2 == 0) ? t1 : t2;
     int in_off[3];
     for (int b2 = 0; b2 < 3; ++b2) in_off[b2] = first ? one[b2] : 0;
     AxisOp op = make_op(a, cur, in_off, cmp, cnt, zero, m, 0, first ? 1 : 0, m, 0);
-    CHECK(axis_op(p, op, src, dst, p->coef_c_fwd));
+    CHECK(launch_axis_op<E>(op, (const E*)src, (E*)dst, (const E*)fwd, p->stream));
     cur = cmp;
     src = dst;
   }
   long long nm = (long long)m * m * (dim == 3 ? m : 1);
-  if (p->esize == 8) CHECK(launch_scale<double>(nm, (double*)src, (const double*)p->dinv0, p->stream));
-  else CHECK(launch_scale<float>(nm, (float*)src, (const float*)p->dinv0, p->stream));
+  CHECK(launch_scale<E>(nm, (E*)src, (const E*)dinv, p->stream));
   // backward: x = (T x .. x T) t into the level interior
   for (int a = 0; a < dim; ++a) {
     const bool last = (a == dim - 1);
-    void* dst = last ? x : (src == p->ctmp1 ? p->ctmp2 : p->ctmp1);
+    void* dst = last ? x : (src == t1 ? t2 : t1);
     Arr out = last ? lev : cmp;
     const int* ooff = last ? one : zero;
     AxisOp op = make_op(a, cur, zero, out, cnt, ooff, m, 0, 0, m, 0);
-    CHECK(axis_op(p, op, src, dst, p->coef_c_bwd));
+    CHECK(launch_axis_op<E>(op, (const E*)src, (E*)dst, (const E*)bwd, p->stream));
     src = dst;
   }
   return GMG_OK;
+}
+
+int coarse_solve(gmg_problem* p, const void* b, void* x) {
+  const LevelGeom& g = p->levels[0].g;
+  if (p->varcoef) {
+    if (p->esize == 8)
+      return launch_dense_solve<double>(g, p->coarse_inv, p->coarse_n, (const double*)b, (double*)x, p->stream);
+    return launch_dense_solve<float>(g, p->coarse_inv, p->coarse_n, (const float*)b, (float*)x, p->stream);
+  }
+  if (p->esize == 4) {  // single-precision problem: the coarse solve runs in FP64
+    const long long n0 = p->levels[0].n_elems;
+    CHECK(launch_convert_f32_f64(n0, (const float*)b, (double*)p->c64_b, p->stream));
+    CHECK(coarse_fd<double>(p, p->c64_b, p->c64_x, p->c64_fwd, p->c64_bwd, p->c64_dinv, p->c64_t1, p->c64_t2));
+    return launch_convert_f64_f32(n0, (const double*)p->c64_x, (float*)x, p->stream);
+  }
+  return coarse_fd<double>(p, b, x, p->coef_c_fwd, p->coef_c_bwd, p->dinv0, p->ctmp1, p->ctmp2);
 }
 
 int vcycle_level(gmg_problem* p, int l, void* x, const void* b) {
@@ -628,6 +643,19 @@ int gmg::detail::create_problem(const gmg_desc* d, gmg_problem* p, const CreateO
   CHECK(upload_table(p, &p->dinv0, d0));
   CHECK(dalloc(p, &p->ctmp1, nm0 * p->esize));
   CHECK(dalloc(p, &p->ctmp2, nm0 * p->esize));
+  if (p->esize == 4) {  // FP64 coarse solve of single-precision problems
+    const size_t es = p->esize;
+    p->esize = 8;
+    int st = upload_table(p, &p->c64_fwd, fwd);
+    if (st == GMG_OK) st = upload_table(p, &p->c64_bwd, bwd);
+    if (st == GMG_OK) st = upload_table(p, &p->c64_dinv, d0);
+    p->esize = es;
+    CHECK(st);
+    CHECK(dalloc(p, &p->c64_t1, nm0 * 8));
+    CHECK(dalloc(p, &p->c64_t2, nm0 * 8));
+    CHECK(dalloc(p, &p->c64_b, p->levels[0].n_elems * 8));
+    CHECK(dalloc(p, &p->c64_x, p->levels[0].n_elems * 8));
+  }
   // outer CG
   if (opt.no_cg) return cudaDeviceSynchronize() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
   const long long nf = p->levels[L - 1].n_elems;

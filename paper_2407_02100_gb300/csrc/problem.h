@@ -63,6 +63,15 @@ struct gmg_problem {
   void* dinv0 = nullptr;       // h0^{2-d} / sum lambda
   void* ctmp1 = nullptr;
   void* ctmp2 = nullptr;
+  // single-precision problems solve the coarsest level in FP64: FP64 copies
+  // of the tables above, temporaries, and the level's b and x
+  void* c64_fwd = nullptr;
+  void* c64_bwd = nullptr;
+  void* c64_dinv = nullptr;
+  void* c64_t1 = nullptr;
+  void* c64_t2 = nullptr;
+  void* c64_b = nullptr;
+  void* c64_x = nullptr;
   // outer CG (double, finest level)
   double* cg_r = nullptr;
   double* cg_z = nullptr;

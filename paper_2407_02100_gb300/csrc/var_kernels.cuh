@@ -173,7 +173,8 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
   constexpr int NINT = DIM == 3 ? M * M * M : M * M;
   constexpr int NE = DIM == 3 ? E * E * E : E * E;
   constexpr int NCELL = 1 << DIM;
-  __shared__ T U[NCLO], R[NINT], RS[NINT], X[NE], P[NE], Q[NE], A1[NE], A2[NE];
+  __shared__ T U[NCLO], R[NINT], RS[NINT];
+  __shared__ T X[NCELL * NE], P[NCELL * NE], Q[NCELL * NE], A1[NCELL * NE], A2[NCELL * NE];
   __shared__ T s_coef[NCELL];
   __shared__ T s_abar, s_theta;
   __shared__ float s_t[8];
@@ -194,7 +195,6 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
     for (int t = threadIdx.x; t < NINT; t += NT) {
       const int x = t % M, y = (t / M) % M, z = DIM == 3 ? t / (M * M) : 0;
       RS[t] = b[origin + 1 + x + py * (y + 1) + (DIM == 3 ? pz * (z + 1) : 0)];
-      R[t] = T(0);
     }
     if (threadIdx.x < NCELL) {
       const int o0 = threadIdx.x & 1, o1 = (threadIdx.x >> 1) & 1, o2 = (threadIdx.x >> 2) & 1;
@@ -212,23 +212,28 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
       s_abar = abar;
       s_theta = min(T(1), T(1.8) * abar / amax);
     }
-    // ---- local residual cell by cell: R = sum_c a_c [A_c u_c]_interior ----
-    for (int c = 0; c < NCELL; ++c) {
+    // ---- local residual: the 2^d cell operators of the patch at once, then
+    // R = sum_c a_c [A_c u_c]_interior node by node (cells in ascending order) ----
+    for (int t = threadIdx.x; t < NCELL * NE; t += NT) {
+      const int c = t / NE, l = t % NE;
       const int o0 = c & 1, o1 = (c >> 1) & 1, o2 = (c >> 2) & 1;
-      for (int t = threadIdx.x; t < NE; t += NT) {
-        const int x = t % E, y = (t / E) % E, z = DIM == 3 ? t / (E * E) : 0;
-        X[t] = U[(o0 * K + x) + C * (o1 * K + y) + (DIM == 3 ? C * C * (o2 * K + z) : 0)];
-      }
-      __syncthreads();
-      cell_operator<DIM, K, NT>(X, P, Q, A1, A2, X, 1, NE);
-      const T ac = s_coef[c];
-      for (int t = threadIdx.x; t < NE; t += NT) {
-        const int px = o0 * K + t % E, py2 = o1 * K + (t / E) % E, pz2 = DIM == 3 ? o2 * K + t / (E * E) : 1;
-        if (px < 1 || px > M || py2 < 1 || py2 > M || (DIM == 3 && (pz2 < 1 || pz2 > M))) continue;
-        R[(px - 1) + M * (py2 - 1) + (DIM == 3 ? M * M * (pz2 - 1) : 0)] += ac * X[t];
-      }
-      __syncthreads();
+      const int x = l % E, y = (l / E) % E, z = DIM == 3 ? l / (E * E) : 0;
+      X[t] = U[(o0 * K + x) + C * (o1 * K + y) + (DIM == 3 ? C * C * (o2 * K + z) : 0)];
     }
+    __syncthreads();
+    cell_operator<DIM, K, NT>(X, P, Q, A1, A2, X, NCELL, NE);
+    for (int t = threadIdx.x; t < NINT; t += NT) {
+      const int x = t % M + 1, y = (t / M) % M + 1, z = DIM == 3 ? t / (M * M) + 1 : 0;  // closure coords
+      T acc = T(0);
+#pragma unroll
+      for (int c = 0; c < NCELL; ++c) {
+        const int lx = x - (c & 1) * K, ly = y - ((c >> 1) & 1) * K, lz = DIM == 3 ? z - ((c >> 2) & 1) * K : 0;
+        if (lx < 0 || lx > K || ly < 0 || ly > K || lz < 0 || lz > K) continue;
+        acc += s_coef[c] * X[c * NE + lx + E * ly + (DIM == 3 ? E * E * lz : 0)];
+      }
+      R[t] = acc;
+    }
+    __syncthreads();
     // ---- reference residual r_ref = h^{2-d} b - R ----
     for (int t = threadIdx.x; t < NINT; t += NT) {
       const T r = sb * RS[t] - R[t];

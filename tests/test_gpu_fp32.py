@@ -80,3 +80,17 @@ def test_mixed_precision_pcg(gmg, dim, k, n, L):
     xo, its, _ = Multigrid(dim, k, n, L).pcg(b, rtol=1e-10)
     assert rel(P32.from_device(u32), xo) < 1e-8
     assert rel(P64.from_device(u64), xo) < 1e-8
+
+
+@pytest.mark.parametrize("dim,k,n", [(3, 4, 4), (2, 3, 8), (3, 2, 6)])
+def test_fp32_problem_solves_the_coarse_level_in_fp64(gmg, dim, k, n):
+    """Single-precision problems keep FP64 for the coarse solve: with a
+    right-hand side that is exactly representable in FP32 the only rounding
+    left is that of the FP32 result (6e-8 relative), whereas an FP32
+    fast-diagonalisation solve would lose about cond(A_0) times more."""
+    P = gmg.Problem(dim, k, n, n_levels=1, precision=gmg.GMG_FP32)
+    b = inputs.random_nodal(dim, k, n, 5101).astype(np.float32).astype(np.float64)
+    x = P.zeros()
+    gmg.gmg_coarse_solve(P.h, P.to_device(b), x)
+    ref = Multigrid(dim, k, n, 1).vcycle(b)
+    assert rel(P.from_device(x), ref) < 3e-7
