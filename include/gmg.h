@@ -185,7 +185,12 @@ int gmg_vcycle(gmg_problem* p, void* x, const void* b);
  * guess on input (a restart resumes from it), solution on output; b: right
  * hand side; both double device vectors.  Stops when ||r|| <= rtol ||b||.
  * stats may be NULL.  Errors: INVALID_ARG, CUDA, NONFINITE, BREAKDOWN,
- * NOT_CONVERGED (u then holds the last iterate). */
+ * NOT_CONVERGED (u then holds the last iterate).  From the second iteration
+ * on, one iteration up to its convergence check (V-cycle, dot products,
+ * direction, FP64 operator, update) is replayed as a CUDA graph captured on
+ * a private stream for this u (kept until u, the coefficient, the local
+ * solver or the slab schedule changes); the host reads back the scalars once
+ * per iteration.  Results are identical to launching the kernels one by one. */
 int cg_gmg_solve(gmg_problem* p, double* u, const double* b, double rtol, int max_it,
                  gmg_solve_stats* stats);
 

@@ -27,6 +27,14 @@ namespace detail {
 
 enum { S_RZ = 0, S_PQ = 1, S_RR = 2, S_RZN = 3, S_BB = 4, S_COUNT = 8 };
 
+void drop_cg_graph(gmg_problem* p) {
+  if (p->cg_exec) cudaGraphExecDestroy(p->cg_exec);
+  if (p->cg_graph) cudaGraphDestroy(p->cg_graph);
+  p->cg_exec = nullptr;
+  p->cg_graph = nullptr;
+  p->cg_graph_u = nullptr;
+}
+
 int dalloc(gmg_problem* p, void** ptr, size_t bytes) {
   *ptr = nullptr;
   if (bytes == 0) bytes = 16;
@@ -522,6 +530,8 @@ int gmg_patch_fd_1d(int k, double* M, double* K, double* T, double* lambda) {
 int gmg_destroy(gmg_problem* p) {
   if (!p) return GMG_OK;
   cudaStreamSynchronize(p->stream);
+  drop_cg_graph(p);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   for (void* ptr : p->owned) cudaFree(ptr);
   delete p;
   return GMG_OK;
@@ -747,6 +757,7 @@ int gmg_smooth_colour(gmg_problem* p, int level, void* u, const void* b, int col
 
 int gmg_set_coefficient(gmg_problem* p, const double* coef) {
   if (!p || !coef) return GMG_ERR_INVALID_ARG;
+  drop_cg_graph(p);
   const int dim = p->desc.dim, k = p->desc.degree, L = (int)p->levels.size();
   if (k > 3) return GMG_ERR_UNSUPPORTED;
   const long long nfine = dim == 3 ? (long long)p->desc.n_cells * p->desc.n_cells * p->desc.n_cells
@@ -802,6 +813,7 @@ int gmg_set_coefficient(gmg_problem* p, const double* coef) {
 
 int gmg_set_local_solver(gmg_problem* p, int solver) {
   if (!p || !p->varcoef) return GMG_ERR_INVALID_ARG;
+  drop_cg_graph(p);
   if (solver == GMG_LOCAL_FD_MEAN) {
     p->local_solver = solver;
     return GMG_OK;
@@ -817,6 +829,7 @@ int gmg_set_local_solver(gmg_problem* p, int solver) {
 
 int gmg_set_slab_width(gmg_problem* p, int width) {
   if (!p || width < -1) return GMG_ERR_INVALID_ARG;
+  drop_cg_graph(p);
   p->slab_width = width;
   for (int l = 0; l < (int)p->levels.size(); ++l) CHECK(build_slabs(p, l, slab_width_for(p, p->levels[l])));
   return cudaDeviceSynchronize() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
@@ -874,6 +887,7 @@ int cg_gmg_solve(gmg_problem* p, double* u, const double* b, double rtol, int ma
   gmg_solve_stats local;
   std::memset(&local, 0, sizeof(local));
   double h_sc[S_COUNT];
+  const cudaStream_t user_stream = s;
   auto fetch = [&]() -> int {
     if (cudaMemcpyAsync(h_sc, sc, sizeof(h_sc), cudaMemcpyDeviceToHost, s) != cudaSuccess) return GMG_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return GMG_ERR_CUDA;
@@ -919,11 +933,22 @@ int cg_gmg_solve(gmg_problem* p, double* u, const double* b, double rtol, int ma
   if (cudaMemcpyAsync(p->cg_p, p->cg_z, n * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return finish(GMG_ERR_CUDA);
   CHECK(launch_dot(n, p->cg_r, p->cg_z, p->partial, sc + S_RZ, s));
-  for (int it = 1; it <= max_it; ++it) {
+  // q = A p, alpha = rz / pq, u += alpha p, r -= alpha q, rr = r.r
+  auto update = [&]() -> int {
     CHECK(cg_apply(p->cg_p, p->cg_q, nullptr, 1.0, 0.0));
     CHECK(launch_dot(n, p->cg_p, p->cg_q, p->partial, sc + S_PQ, s));
-    CHECK(launch_cg_update(n, u, p->cg_r, p->cg_p, p->cg_q, sc + S_RZ, sc + S_PQ, p->partial,
-                           sc + S_RR, s));
+    return launch_cg_update(n, u, p->cg_r, p->cg_p, p->cg_q, sc + S_RZ, sc + S_PQ, p->partial, sc + S_RR, s);
+  };
+  // z = V(r), beta = rz_new / rz, p = z + beta p, then the update
+  auto iteration_body = [&]() -> int {
+    CHECK(precondition());
+    CHECK(launch_dot(n, p->cg_r, p->cg_z, p->partial, sc + S_RZN, s));
+    CHECK(launch_cg_direction(n, p->cg_p, p->cg_z, sc + S_RZN, sc + S_RZ, s));
+    if (cudaMemcpyAsync(sc + S_RZ, sc + S_RZN, 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return GMG_ERR_CUDA;
+    return update();
+  };
+  CHECK(update());
+  for (int it = 1; it <= max_it; ++it) {
     CHECK(fetch());
     if (!std::isfinite(h_sc[S_RZ]) || !std::isfinite(h_sc[S_PQ]) || !std::isfinite(h_sc[S_RR]))
       return finish(GMG_ERR_NONFINITE);
@@ -937,11 +962,41 @@ int cg_gmg_solve(gmg_problem* p, double* u, const double* b, double rtol, int ma
       local.converged = 1;
       return finish(GMG_OK);
     }
-    CHECK(precondition());
-    CHECK(launch_dot(n, p->cg_r, p->cg_z, p->partial, sc + S_RZN, s));
-    CHECK(launch_cg_direction(n, p->cg_p, p->cg_z, sc + S_RZN, sc + S_RZ, s));
-    if (cudaMemcpyAsync(sc + S_RZ, sc + S_RZN, 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-      return finish(GMG_ERR_CUDA);
+    if (it == max_it) break;
+    // next iteration up to its convergence check: a CUDA graph replay
+    // (captured once the first iteration has prepared every kernel)
+    if (!p->cg_exec || p->cg_graph_u != u) {
+      drop_cg_graph(p);
+      if (!p->cap_stream && cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return finish(GMG_ERR_CUDA);
+      const long long before = launch_count();
+      s = p->stream = p->cap_stream;  // the caller's stream may be the legacy one
+      int cst = GMG_OK;
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cst = GMG_ERR_CUDA;
+      } else {
+        cst = iteration_body();
+        if (cudaStreamEndCapture(s, &g) != cudaSuccess || !g) cst = cst == GMG_OK ? GMG_ERR_CUDA : cst;
+      }
+      s = p->stream = user_stream;
+      const long long captured = launch_count() - before;
+      count_launch((int)-captured);  // captured launches run with the graph
+      if (cst != GMG_OK) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return finish(cst);
+      }
+      p->cg_graph = g;
+      if (cudaGraphInstantiate(&p->cg_exec, g, 0) != cudaSuccess) {
+        drop_cg_graph(p);
+        return finish(GMG_ERR_CUDA);
+      }
+      p->cg_graph_u = u;
+      p->cg_graph_kernels = captured;
+    }
+    if (cudaGraphLaunch(p->cg_exec, s) != cudaSuccess) return finish(GMG_ERR_CUDA);
+    count_launch((int)p->cg_graph_kernels);
   }
   return finish(GMG_ERR_NOT_CONVERGED);
 }

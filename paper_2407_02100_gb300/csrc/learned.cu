@@ -500,6 +500,7 @@ int gmg_learned_train(gmg_problem* p, int n_samples, const int* sample_vertices,
                       int* kept_patches) {
   if (!p || !p->varcoef || n_samples < 1 || !sample_vertices || !residuals || steps < 0 || batch < 1)
     return GMG_ERR_INVALID_ARG;
+  drop_cg_graph(p);
   const int dim = p->desc.dim, k = p->desc.degree, L = (int)p->levels.size();
   const Shape sh = make_shape(dim, k, kRank, kHidden);
   if (exact_smem(sh) > 220 * 1024) return GMG_ERR_UNSUPPORTED;

@@ -93,6 +93,15 @@ struct gmg_problem {
   // skewed-slab schedule request: 0 whole colours, > 0 slab width in
   // vertex rows, -1 chosen per level to fit L2 (gmg_set_slab_width)
   int slab_width = 0;
+  // CUDA graph of one outer-CG iteration (V-cycle preconditioner, dot
+  // products, direction, FP64 operator, update) for the solution vector
+  // cg_graph_u, captured on a private stream; dropped whenever anything the
+  // V-cycle launches changes
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t cg_graph = nullptr;
+  cudaGraphExec_t cg_exec = nullptr;
+  const void* cg_graph_u = nullptr;
+  long long cg_graph_kernels = 0;
 };
 
 namespace gmg {
@@ -105,6 +114,8 @@ namespace detail {
   } while (0)
 
 int dalloc(gmg_problem* p, void** ptr, size_t bytes);
+// forget the captured outer-CG iteration (anything the V-cycle launches changed)
+void drop_cg_graph(gmg_problem* p);
 LevelGeom make_geom(int dim, int k, int n);
 long long geom_elems(const LevelGeom& g);
 double op_scale(const Level& L);  // h^{d-2}
