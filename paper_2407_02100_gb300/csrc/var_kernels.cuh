@@ -176,6 +176,9 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
   __shared__ T U[NCLO], R[NINT], RS[NINT];
   __shared__ T X[NCELL * NE], P[NCELL * NE], Q[NCELL * NE], A1[NCELL * NE], A2[NCELL * NE];
   __shared__ T s_coef[NCELL];
+  // the patch's correction block (U then s), prefetched while the residual
+  // and the FD solve are computed (rank <= 4)
+  __shared__ float s_corr[NINT * 4 + 4];
   __shared__ T s_abar, s_theta;
   __shared__ float s_t[8];
   const long long py = pl.g.py, pz = pl.g.pz;
@@ -188,6 +191,14 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
     const int i2 = DIM == 3 ? rest / pl.count[1] : 0;
     const int v0 = pl.first[0] + 2 * i0, v1 = pl.first[1] + 2 * i1, v2 = DIM == 3 ? pl.first[2] + 2 * i2 : 1;
     const long long origin = (long long)(v0 - 1) * K + py * ((v1 - 1) * K) + (DIM == 3 ? pz * ((v2 - 1) * K) : 0);
+    if (corr) {
+      const int vid = (v0 - 1) + (n - 1) * ((v1 - 1) + (DIM == 3 ? (n - 1) * (v2 - 1) : 0));
+      const float* Up = corr + (long long)vid * (NINT * rank + rank);
+      for (int i = threadIdx.x; i < NINT * rank + rank; i += NT)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(async::smem_u32(s_corr + i)), "l"(Up + i)
+                     : "memory");
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
     for (int t = threadIdx.x; t < NCLO; t += NT) {
       const int x = t % C, y = (t / C) % C, z = DIM == 3 ? t / (C * C) : 0;
       U[t] = u[origin + x + py * y + pz * z];
@@ -260,10 +271,11 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
       }
       __syncthreads();
     }
-    // ---- learned rank-R correction U diag(s) U^T r_ref ----
+    // ---- learned rank-R correction U diag(s) U^T r_ref (block prefetched) ----
     if (corr) {
-      const int vid = (v0 - 1) + (n - 1) * ((v1 - 1) + (DIM == 3 ? (n - 1) * (v2 - 1) : 0));
-      const float* Up = corr + (long long)vid * (NINT * rank + rank);
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      __syncthreads();
+      const float* Up = s_corr;
       const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
       for (int q = warp; q < rank; q += NT / 32) {
         float acc = 0.f;
