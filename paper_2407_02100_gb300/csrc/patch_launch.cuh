@@ -1,13 +1,11 @@
 // Launchers for one scalar type; included after patch_kernels.cuh by
 // patch_f64.cu / patch_f32.cu.
 #pragma once
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
 #include <algorithm>
 #include <vector>
 
 #include "../../include/gmg.h"
+#include "tma_host.h"
 
 namespace gmg {
 namespace GMG_NS {
@@ -70,49 +68,15 @@ static inline int table_groups(PatchTable& tab, int ppc) {
   return g;
 }
 
-// ---- TMA gather: tensor maps of the level vectors ----
-static PFN_cuTensorMapEncodeTiled_v12000 tma_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-    else
-      cudaGetLastError();
-  }
-  return fn;
-}
-
-// A vector can be read by the TMA boxes when its base is 16-byte aligned and
-// its row and plane pitches are multiples of 16 bytes.
+// ---- TMA gather: every vector of the table must allow the boxes ----
 static bool tma_usable(const PatchTable& tab, int dim) {
-  if (!tma_encoder()) return false;
   for (int i = 0; i < tab.n; ++i) {
     const PatchEntry& e = tab.e[i];
-    if (((uintptr_t)e.u | (uintptr_t)e.b) & 15) return false;
-    if ((e.py * (long long)sizeof(T)) % 16 || (dim == 3 && (e.pz * (long long)sizeof(T)) % 16)) return false;
-    if (e.N < 2) return false;
+    if (e.N < 2 || !tma_vector_ok(e.u, (int)sizeof(T), dim, e.py, e.pz) ||
+        !tma_vector_ok(e.b, (int)sizeof(T), dim, e.py, e.pz))
+      return false;
   }
   return true;
-}
-
-// box {XU, rows, rows[, rows]} over the lattice {N, N[, N]} of one vector
-static bool tma_encode(CUtensorMap* m, const void* ptr, int dim, int N, long long py, long long pz, int xbox,
-                       int rows) {
-  const cuuint64_t gdim[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)N};
-  const cuuint64_t gstride[2] = {(cuuint64_t)(py * (long long)sizeof(T)), (cuuint64_t)(pz * (long long)sizeof(T))};
-  const cuuint32_t box[3] = {(cuuint32_t)xbox, (cuuint32_t)rows, (cuuint32_t)rows};
-  const cuuint32_t estride[3] = {1, 1, 1};
-  const CUresult r = tma_encoder()(m, sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                                   (cuuint32_t)dim, const_cast<void*>(ptr), gdim, gstride, box, estride,
-                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
 }
 
 template <int DIM, int K, int PPC, int NT, int NBUF, int ME>
@@ -134,8 +98,8 @@ static int launch_table_cfg(PatchTable& tab, const T* dinv, cudaStream_t s) {
   if constexpr (ME > 0) {
     for (int i = 0; i < tab.n; ++i) {
       const PatchEntry& e = tab.e[i];
-      if (!tma_encode(&maps.u[i], e.u, DIM, e.N, e.py, e.pz, Z::XU, Z::C) ||
-          !tma_encode(&maps.b[i], e.b, DIM, e.N, e.py, e.pz, Z::XB, Z::M))
+      if (!tma_encode(&maps.u[i], e.u, (int)sizeof(T), DIM, e.N, e.py, e.pz, Z::XU, Z::C) ||
+          !tma_encode(&maps.b[i], e.b, (int)sizeof(T), DIM, e.N, e.py, e.pz, Z::XB, Z::M))
         return GMG_ERR_CUDA;
     }
   }

@@ -161,19 +161,29 @@ __global__ void init_interior_kernel(T* __restrict__ y, const T* __restrict__ b,
   }
 }
 
-// One colour of the variable-coefficient patch smoother, one patch per CTA.
-template <int DIM, int K, int NT>
+// One colour of the variable-coefficient patch smoother: persistent CTAs,
+// one patch at a time.  With TMA the closure of u and the interior of b of
+// the CTA's next patch arrive by two TMA boxes (as in patch_colour_kernel)
+// into the other input slot while the current patch is computed; without it
+// they are read element by element into the same layout.
+template <int DIM, int K, int NT, bool TMA>
 __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const T* __restrict__ b,
                                                        const T* __restrict__ coef,
                                                        const T* __restrict__ dinv,
                                                        const float* __restrict__ corr, int rank,
-                                                       PatchLaunch pl) {
-  constexpr int C = 2 * K + 1, M = 2 * K - 1, E = K + 1;
-  constexpr int NCLO = DIM == 3 ? C * C * C : C * C;
+                                                       PatchLaunch pl,
+                                                       const __grid_constant__ TmaMaps<TMA ? 1 : 0> maps,
+                                                       int* __restrict__ err) {
+  using Z = SweepSmem<DIM, K, TMA>;
+  constexpr int C = 2 * K + 1, M = 2 * K - 1, E = K + 1, XU = Z::XU, XB = Z::XB;
   constexpr int NINT = DIM == 3 ? M * M * M : M * M;
   constexpr int NE = DIM == 3 ? E * E * E : E * E;
   constexpr int NCELL = 1 << DIM;
-  __shared__ T U[NCLO], R[NINT], RS[NINT];
+  // input slots: closure of u (rows of XU), then interior of b (rows of XB)
+  __shared__ __align__(128) T IN[TMA ? 2 : 1][Z::IN];
+  __shared__ T R[NINT], RS[NINT];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ int s_shift[2];
   __shared__ T X[NCELL * NE], P[NCELL * NE], Q[NCELL * NE], A1[NCELL * NE], A2[NCELL * NE];
   __shared__ T s_coef[NCELL];
   // the patch's correction block (U then s), prefetched while the residual
@@ -184,13 +194,51 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
   const long long py = pl.g.py, pz = pl.g.pz;
   const int n = pl.g.n;
   const T sb = (T)pl.sb, om = (T)pl.omega;
-  for (int pid = blockIdx.x; pid < pl.n_patches; pid += gridDim.x) {
+  // vertex of patch pid of the colour
+  auto vertex = [&](int pid, int& v0, int& v1, int& v2) {
     const int i0 = pid % pl.count[0];
     const int rest = pid / pl.count[0];
     const int i1 = rest % pl.count[1];
     const int i2 = DIM == 3 ? rest / pl.count[1] : 0;
-    const int v0 = pl.first[0] + 2 * i0, v1 = pl.first[1] + 2 * i1, v2 = DIM == 3 ? pl.first[2] + 2 * i2 : 1;
+    v0 = pl.first[0] + 2 * i0;
+    v1 = pl.first[1] + 2 * i1;
+    v2 = DIM == 3 ? pl.first[2] + 2 * i2 : 1;
+  };
+  auto uo = [](int x, int y, int z) { return DIM == 3 ? (z * C + y) * XU + x : y * XU + x; };
+  auto bo = [](int x, int y, int z) { return DIM == 3 ? (z * M + y) * XB + x : y * XB + x; };
+  // TMA boxes of patch pid into slot (one thread)
+  auto issue = [&](int pid, int slot) {
+    if constexpr (TMA) {
+      int v0, v1, v2;
+      vertex(pid, v0, v1, v2);
+      const int x0 = (v0 - 1) * K, y0 = (v1 - 1) * K, z0 = DIM == 3 ? (v2 - 1) * K : 0;
+      const int xa = x0 - x0 % Z::A;
+      s_shift[slot] = x0 - xa;
+      async::mbar_arrive_expect_tx(&s_bar[slot], (uint32_t)(Z::BOX_U + Z::BOX_B));
+      if (DIM == 3) {
+        async::tma_load_3d(IN[slot], &maps.u[0], xa, y0, z0, &s_bar[slot]);
+        async::tma_load_3d(IN[slot] + Z::NCLO, &maps.b[0], xa, y0 + 1, z0 + 1, &s_bar[slot]);
+      } else {
+        async::tma_load_2d(IN[slot], &maps.u[0], xa, y0, &s_bar[slot]);
+        async::tma_load_2d(IN[slot] + Z::NCLO, &maps.b[0], xa, y0 + 1, &s_bar[slot]);
+      }
+    }
+  };
+  uint32_t phase = 0;
+  bool wait_ok = true;
+  if (TMA && threadIdx.x == 0) {
+    async::mbar_init(&s_bar[0], 1);
+    async::mbar_init(&s_bar[1], 1);
+    if ((int)blockIdx.x < pl.n_patches) issue(blockIdx.x, 0);
+  }
+  if (TMA) __syncthreads();  // barriers initialised before anyone waits on them
+  int it = 0;
+  for (int pid = blockIdx.x; pid < pl.n_patches; pid += gridDim.x, ++it) {
+    const int cur = TMA ? (it & 1) : 0;
+    int v0, v1, v2;
+    vertex(pid, v0, v1, v2);
     const long long origin = (long long)(v0 - 1) * K + py * ((v1 - 1) * K) + (DIM == 3 ? pz * ((v2 - 1) * K) : 0);
+    if (TMA && threadIdx.x == 0 && pid + (int)gridDim.x < pl.n_patches) issue(pid + gridDim.x, cur ^ 1);
     if (corr) {
       const int vid = (v0 - 1) + (n - 1) * ((v1 - 1) + (DIM == 3 ? (n - 1) * (v2 - 1) : 0));
       const float* Up = corr + (long long)vid * (NINT * rank + rank);
@@ -199,13 +247,18 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
                      : "memory");
       asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
-    for (int t = threadIdx.x; t < NCLO; t += NT) {
-      const int x = t % C, y = (t / C) % C, z = DIM == 3 ? t / (C * C) : 0;
-      U[t] = u[origin + x + py * y + pz * z];
-    }
-    for (int t = threadIdx.x; t < NINT; t += NT) {
-      const int x = t % M, y = (t / M) % M, z = DIM == 3 ? t / (M * M) : 0;
-      RS[t] = b[origin + 1 + x + py * (y + 1) + (DIM == 3 ? pz * (z + 1) : 0)];
+    if constexpr (!TMA) {  // element-wise gather into the slot layout (XU = C, XB = M)
+      for (int t = threadIdx.x; t < (DIM == 3 ? C * C * C : C * C); t += NT) {
+        const int x = t % C, y = (t / C) % C, z = DIM == 3 ? t / (C * C) : 0;
+        IN[0][t] = u[origin + x + py * y + pz * z];
+      }
+      for (int t = threadIdx.x; t < NINT; t += NT) {
+        const int x = t % M, y = (t / M) % M, z = DIM == 3 ? t / (M * M) : 0;
+        IN[0][Z::NCLO + t] = b[origin + 1 + x + py * (y + 1) + (DIM == 3 ? pz * (z + 1) : 0)];
+      }
+    } else {
+      if (wait_ok && !async::mbar_wait(&s_bar[cur], (phase >> cur) & 1u)) wait_ok = false;
+      phase ^= 1u << cur;
     }
     if (threadIdx.x < NCELL) {
       const int o0 = threadIdx.x & 1, o1 = (threadIdx.x >> 1) & 1, o2 = (threadIdx.x >> 2) & 1;
@@ -213,6 +266,8 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
       s_coef[threadIdx.x] = coef[c];
     }
     __syncthreads();
+    const T* const U = IN[cur] + (TMA ? s_shift[cur] : 0);                   // closure (x, y, z)
+    const T* const Bv = IN[cur] + Z::NCLO + (TMA ? s_shift[cur] + 1 : 0);   // interior of b
     if (threadIdx.x == 0) {
       T lg = T(0), amax = s_coef[0];
       for (int c = 0; c < NCELL; ++c) {
@@ -229,7 +284,7 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
       const int c = t / NE, l = t % NE;
       const int o0 = c & 1, o1 = (c >> 1) & 1, o2 = (c >> 2) & 1;
       const int x = l % E, y = (l / E) % E, z = DIM == 3 ? l / (E * E) : 0;
-      X[t] = U[(o0 * K + x) + C * (o1 * K + y) + (DIM == 3 ? C * C * (o2 * K + z) : 0)];
+      X[t] = U[uo(o0 * K + x, o1 * K + y, DIM == 3 ? o2 * K + z : 0)];
     }
     __syncthreads();
     cell_operator<DIM, K, NT>(X, P, Q, A1, A2, X, NCELL, NE);
@@ -247,7 +302,7 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
     __syncthreads();
     // ---- reference residual r_ref = h^{2-d} b - R ----
     for (int t = threadIdx.x; t < NINT; t += NT) {
-      const T r = sb * RS[t] - R[t];
+      const T r = sb * Bv[bo(t % M, (t / M) % M, DIM == 3 ? t / (M * M) : 0)] - R[t];
       RS[t] = r;
       R[t] = r;
     }
@@ -298,8 +353,10 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
       const long long gi = origin + 1 + x + py * (y + 1) + (DIM == 3 ? pz * (z + 1) : 0);
       u[gi] = fma(scale, R[t], u[gi]);
     }
+    if (TMA) async::fence_proxy_async();  // slot reads before the next TMA writes into it
     __syncthreads();
   }
+  if (TMA && !wait_ok) atomicExch(err, GMG_ERR_TIMEOUT);
 }
 
 }  // namespace GMG_NS

@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "../../include/gmg.h"
+#include "tma_host.h"
 
 namespace gmg {
 namespace GMG_NS {
@@ -30,12 +31,45 @@ static int apply_var_impl(const LevelGeom& g, long long n_elems, const T* x, T* 
   return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
 }
 
+// persistent grid of the variable-coefficient sweep kernel (resident CTAs per SM)
+template <int DIM, int K, bool TMA>
+static int var_grid(int n_patches) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    int dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, patch_var_kernel<DIM, K, kVarThreads, TMA>,
+                                                      kVarThreads, 0) != cudaSuccess ||
+        per_sm <= 0 || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return -1;
+    per_sm *= sms;
+  }
+  return std::min(n_patches, per_sm);
+}
+
 template <int DIM, int K>
 static int patch_var_impl(const PatchLaunch& pl, T* u, const T* b, const T* coef, const T* dinv,
                           const float* corr, int rank, cudaStream_t s) {
   if (pl.n_patches <= 0) return GMG_OK;
-  const int grid = std::min(pl.n_patches, 152 * 16);
-  patch_var_kernel<DIM, K, kVarThreads><<<grid, kVarThreads, 0, s>>>(u, b, coef, dinv, corr, rank, pl);
+  int* const flag = device_wait_flag();
+  if (!flag) return GMG_ERR_CUDA;
+  const int es = (int)sizeof(T);
+  if (tma_vector_ok(u, es, DIM, pl.g.py, pl.g.pz) && tma_vector_ok(b, es, DIM, pl.g.py, pl.g.pz)) {
+    using Z = SweepSmem<DIM, K, true>;
+    TmaMaps<1> maps;
+    if (!tma_encode(&maps.u[0], u, es, DIM, pl.g.N, pl.g.py, pl.g.pz, Z::XU, Z::C) ||
+        !tma_encode(&maps.b[0], b, es, DIM, pl.g.N, pl.g.py, pl.g.pz, Z::XB, Z::M))
+      return GMG_ERR_CUDA;
+    const int grid = var_grid<DIM, K, true>(pl.n_patches);
+    if (grid <= 0) return GMG_ERR_CUDA;
+    patch_var_kernel<DIM, K, kVarThreads, true><<<grid, kVarThreads, 0, s>>>(u, b, coef, dinv, corr, rank, pl,
+                                                                             maps, flag);
+  } else {
+    const int grid = var_grid<DIM, K, false>(pl.n_patches);
+    if (grid <= 0) return GMG_ERR_CUDA;
+    patch_var_kernel<DIM, K, kVarThreads, false><<<grid, kVarThreads, 0, s>>>(u, b, coef, dinv, corr, rank, pl,
+                                                                              TmaMaps<0>(), flag);
+  }
   count_launch();
   return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
 }
