@@ -180,3 +180,49 @@ def test_tma_and_elementwise_gathers_agree(gmg, dim, k, n, prec):
     ref = PatchSmoother(Mesh(dim, k, n)).sweep(u0, b)
     got = P.from_device(ua)
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < (1e-12 if prec == 0 else 1e-5)
+
+
+# degenerate meshes: one interior vertex per direction, so a single patch in
+# the last colour and empty launches for every other colour
+@pytest.mark.parametrize("dim,k,n", [(2, 3, 2), (3, 2, 2), (3, 4, 2)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_single_patch_mesh(gmg, dim, k, n, prec):
+    m = Mesh(dim, k, n)
+    P = gmg.Problem(dim, k, n, n_levels=1, precision=prec)
+    u0 = inputs.random_nodal(dim, k, n, 5201)
+    b = inputs.random_nodal(dim, k, n, 5202)
+    ud = P.to_device(u0)
+    gmg.gmg_smooth(P.h, 0, ud, P.to_device(b), 1, False)
+    close(P.from_device(ud), PatchSmoother(m).sweep(u0, b), 1e-12 if prec == 0 else 1e-5, "single patch")
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)])
+def test_full_size_colour_step_on_sampled_patches(gmg, prec, tol):
+    """3D Q4 on 64^3 cells (16,974,593 nodes), the bench's workload and launch
+    configuration: one colour step on the GPU, then 40 sampled patches of
+    that colour recomputed one by one by the oracle (dense local solve of the
+    patch block built from the same inputs).  Nodes outside the colour's
+    patch interiors must be untouched."""
+    dim, k, n, colour = 3, 4, 64, 5
+    m = Mesh(dim, k, n)
+    P = gmg.Problem(dim, k, n, n_levels=1, precision=prec)
+    u0 = inputs.random_nodal(dim, k, n, 5301)
+    b = inputs.random_nodal(dim, k, n, 5302)
+    if prec == 1:   # the FP32 kernel sees these values: the oracle takes the same
+        u0 = u0.astype(np.float32).astype(np.float64)
+        b = b.astype(np.float32).astype(np.float64)
+    ud = P.to_device(u0)
+    gmg.gmg_smooth_colour(P.h, 0, ud, P.to_device(b), colour)
+    got = P.from_device(ud)
+    V = m.vertices_of_colour(colour)
+    rng = np.random.default_rng(5303)
+    sample = V[rng.choice(len(V), 40, replace=False)]
+    Abar, inner = m.patch_block()
+    Aj = Abar[:, inner]
+    clo, inn = m.closure_index(sample), m.interior_index(sample)
+    r = b[inn] - u0[clo] @ Abar.T
+    ref = u0[inn] + np.linalg.solve(Aj, r.T).T
+    close(got[inn].ravel(), ref.ravel(), tol, "sampled patches")
+    touched = np.zeros(m.n_nodes, dtype=bool)
+    touched[m.interior_index(V).ravel()] = True
+    assert np.array_equal(got[~touched], u0[~touched])
