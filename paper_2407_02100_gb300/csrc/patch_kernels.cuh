@@ -524,119 +524,122 @@ __device__ __forceinline__ T cell_row(int o, const T (&x)[EI]) {
   return acc;
 }
 
-template <int DIM, int K, int BC>
+// Tile of BX x BY (x BZ) cells: inputs E?I = (B? + 1) K + 1 nodes per
+// direction (one halo cell below), outputs E?O = B? K.
+template <int DIM, int K, int BX, int BY, int BZ>
 struct ApplyDims {
-  static constexpr int EI = (BC + 1) * K + 1;
-  static constexpr int EO = BC * K;
-  static constexpr int SA = DIM == 3 ? cmax(EI * EI * EI, 2 * EI * EO * EO) : EI * EI;
-  static constexpr int SB = DIM == 3 ? 2 * EI * EI * EO : 2 * EI * EO;
+  static constexpr int EIX = (BX + 1) * K + 1, EIY = (BY + 1) * K + 1, EIZ = DIM == 3 ? (BZ + 1) * K + 1 : 1;
+  static constexpr int EOX = BX * K, EOY = BY * K, EOZ = DIM == 3 ? BZ * K : 1;
+  // A: the input tile, later the stage-y results; B: the stage-z results
+  static constexpr int SA = DIM == 3 ? cmax(EIX * EIY * EIZ, 2 * EIX * EOY * EOZ) : EIX * EIY;
+  static constexpr int SB = DIM == 3 ? 2 * EIX * EIY * EOZ : 2 * EIX * EOY;
   static constexpr int SMEM_BYTES = (SA + SB) * (int)sizeof(T);
 };
 
-template <int DIM, int K, int BC, int NT>
+template <int DIM, int K, int BX, int BY, int BZ, int NT>
 __global__ void __launch_bounds__(NT) apply_kernel(const T* __restrict__ xin, T* __restrict__ y,
                                                    const T* __restrict__ bvec, ApplyLaunch al) {
-  using D = ApplyDims<DIM, K, BC>;
-  constexpr int EI = D::EI, EO = D::EO;
+  using D = ApplyDims<DIM, K, BX, BY, BZ>;
+  constexpr int EIX = D::EIX, EIY = D::EIY, EIZ = D::EIZ, EOX = D::EOX, EOY = D::EOY, EOZ = D::EOZ;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);
   T* B = A + D::SA;
   const int N = al.g.N, n = al.g.n;
   const long long py = al.g.py, pz = al.g.pz;
-  const int tiles = (n + BC - 1) / BC;
-  const int ntile = DIM == 3 ? tiles * tiles * tiles : tiles * tiles;
+  const int tx = (n + BX - 1) / BX, ty = (n + BY - 1) / BY, tz = DIM == 3 ? (n + BZ - 1) / BZ : 1;
+  const int ntile = tx * ty * tz;
   const T alpha = (T)al.alpha, beta = (T)al.beta;
 
   for (int tid = blockIdx.x; tid < ntile; tid += gridDim.x) {
-    const int t0 = tid % tiles, t1 = (tid / tiles) % tiles, t2 = DIM == 3 ? tid / (tiles * tiles) : 0;
-    const int g0 = (t0 * BC - 1) * K, g1 = (t1 * BC - 1) * K, g2 = DIM == 3 ? (t2 * BC - 1) * K : 0;
+    const int t0 = tid % tx, t1 = (tid / tx) % ty, t2 = DIM == 3 ? tid / (tx * ty) : 0;
+    const int g0 = (t0 * BX - 1) * K, g1 = (t1 * BY - 1) * K, g2 = DIM == 3 ? (t2 * BZ - 1) * K : 0;
     // gather the tile with zero fill outside the lattice
-    const int nin = DIM == 3 ? EI * EI * EI : EI * EI;
+    const int nin = EIX * EIY * EIZ;
     for (int t = threadIdx.x; t < nin; t += NT) {
-      int x = t % EI, yy = (t / EI) % EI, z = DIM == 3 ? t / (EI * EI) : 0;
+      int x = t % EIX, yy = (t / EIX) % EIY, z = DIM == 3 ? t / (EIX * EIY) : 0;
       int gx = g0 + x, gy = g1 + yy, gz = g2 + z;
       bool ok = gx >= 0 && gx < N && gy >= 0 && gy < N && (DIM == 2 || (gz >= 0 && gz < N));
       A[t] = ok ? xin[gx + py * gy + pz * gz] : T(0);
     }
     __syncthreads();
     if (DIM == 3) {
-      // stage z: P = M_z x, Q = K_z x   (x:EI, y:EI, z:EO)
-      for (int l = threadIdx.x; l < EI * EI; l += NT) {
-        T v[EI];
+      // stage z: P = M_z x, Q = K_z x   (x:EIX, y:EIY, z:EOZ)
+      for (int l = threadIdx.x; l < EIX * EIY; l += NT) {
+        T v[EIZ];
 #pragma unroll
-        for (int j = 0; j < EI; ++j) v[j] = A[l + j * EI * EI];
+        for (int j = 0; j < EIZ; ++j) v[j] = A[l + j * EIX * EIY];
 #pragma unroll
-        for (int o = 0; o < EO; ++o) {
-          B[l + o * EI * EI] = cell_row<K, EI, 0>(o, v);
-          B[EI * EI * EO + l + o * EI * EI] = cell_row<K, EI, 1>(o, v);
+        for (int o = 0; o < EOZ; ++o) {
+          B[l + o * EIX * EIY] = cell_row<K, EIZ, 0>(o, v);
+          B[EIX * EIY * EOZ + l + o * EIX * EIY] = cell_row<K, EIZ, 1>(o, v);
         }
       }
       __syncthreads();
-      // stage y: A1 = M_y P, A2 = K_y P + M_y Q   (x:EI, y:EO, z:EO)
-      for (int l = threadIdx.x; l < EI * EO; l += NT) {
-        int x0 = l % EI, z = l / EI;
-        T p[EI], q[EI];
+      // stage y: A1 = M_y P, A2 = K_y P + M_y Q   (x:EIX, y:EOY, z:EOZ)
+      for (int l = threadIdx.x; l < EIX * EOZ; l += NT) {
+        int x0 = l % EIX, z = l / EIX;
+        T p[EIY], q[EIY];
 #pragma unroll
-        for (int j = 0; j < EI; ++j) {
-          p[j] = B[x0 + j * EI + z * EI * EI];
-          q[j] = B[EI * EI * EO + x0 + j * EI + z * EI * EI];
+        for (int j = 0; j < EIY; ++j) {
+          p[j] = B[x0 + j * EIX + z * EIX * EIY];
+          q[j] = B[EIX * EIY * EOZ + x0 + j * EIX + z * EIX * EIY];
         }
 #pragma unroll
-        for (int o = 0; o < EO; ++o) {
-          A[x0 + o * EI + z * EI * EO] = cell_row<K, EI, 0>(o, p);
-          A[EI * EO * EO + x0 + o * EI + z * EI * EO] = cell_row<K, EI, 1>(o, p) + cell_row<K, EI, 0>(o, q);
+        for (int o = 0; o < EOY; ++o) {
+          A[x0 + o * EIX + z * EIX * EOY] = cell_row<K, EIY, 0>(o, p);
+          A[EIX * EOY * EOZ + x0 + o * EIX + z * EIX * EOY] = cell_row<K, EIY, 1>(o, p) + cell_row<K, EIY, 0>(o, q);
         }
       }
       __syncthreads();
       // stage x and write: y = alpha (K_x A1 + M_x A2) + beta b on owned interior nodes
-      for (int l = threadIdx.x; l < EO * EO; l += NT) {
-        int yy = l % EO, z = l / EO;
+      for (int l = threadIdx.x; l < EOY * EOZ; l += NT) {
+        int yy = l % EOY, z = l / EOY;
         int gy = g1 + K + yy, gz = g2 + K + z;
         if (gy <= 0 || gy >= N - 1 || gz <= 0 || gz >= N - 1) continue;
-        T a1[EI], a2[EI];
+        T a1[EIX], a2[EIX];
 #pragma unroll
-        for (int j = 0; j < EI; ++j) {
-          a1[j] = A[j + EI * (yy + EO * z)];
-          a2[j] = A[EI * EO * EO + j + EI * (yy + EO * z)];
+        for (int j = 0; j < EIX; ++j) {
+          a1[j] = A[j + EIX * (yy + EOY * z)];
+          a2[j] = A[EIX * EOY * EOZ + j + EIX * (yy + EOY * z)];
         }
         const long long row = py * gy + pz * gz;
 #pragma unroll
-        for (int o = 0; o < EO; ++o) {
+        for (int o = 0; o < EOX; ++o) {
           int gx = g0 + K + o;
           if (gx <= 0 || gx >= N - 1) continue;
-          T v = alpha * (cell_row<K, EI, 1>(o, a1) + cell_row<K, EI, 0>(o, a2));
+          T v = alpha * (cell_row<K, EIX, 1>(o, a1) + cell_row<K, EIX, 0>(o, a2));
           if (bvec) v += beta * bvec[row + gx];
           y[row + gx] = v;
         }
       }
     } else {
-      // stage y: P = M_y x, Q = K_y x   (x:EI, y:EO)
-      for (int l = threadIdx.x; l < EI; l += NT) {
-        T v[EI];
+      // stage y: P = M_y x, Q = K_y x   (x:EIX, y:EOY)
+      for (int l = threadIdx.x; l < EIX; l += NT) {
+        T v[EIY];
 #pragma unroll
-        for (int j = 0; j < EI; ++j) v[j] = A[l + j * EI];
+        for (int j = 0; j < EIY; ++j) v[j] = A[l + j * EIX];
 #pragma unroll
-        for (int o = 0; o < EO; ++o) {
-          B[l + o * EI] = cell_row<K, EI, 0>(o, v);
-          B[EI * EO + l + o * EI] = cell_row<K, EI, 1>(o, v);
+        for (int o = 0; o < EOY; ++o) {
+          B[l + o * EIX] = cell_row<K, EIY, 0>(o, v);
+          B[EIX * EOY + l + o * EIX] = cell_row<K, EIY, 1>(o, v);
         }
       }
       __syncthreads();
-      for (int l = threadIdx.x; l < EO; l += NT) {
+      for (int l = threadIdx.x; l < EOY; l += NT) {
         int gy = g1 + K + l;
         if (gy <= 0 || gy >= N - 1) continue;
-        T p[EI], q[EI];
+        T p[EIX], q[EIX];
 #pragma unroll
-        for (int j = 0; j < EI; ++j) {
-          p[j] = B[j + EI * l];
-          q[j] = B[EI * EO + j + EI * l];
+        for (int j = 0; j < EIX; ++j) {
+          p[j] = B[j + EIX * l];
+          q[j] = B[EIX * EOY + j + EIX * l];
         }
         const long long row = py * gy;
 #pragma unroll
-        for (int o = 0; o < EO; ++o) {
+        for (int o = 0; o < EOX; ++o) {
           int gx = g0 + K + o;
           if (gx <= 0 || gx >= N - 1) continue;
-          T v = alpha * (cell_row<K, EI, 1>(o, p) + cell_row<K, EI, 0>(o, q));
+          T v = alpha * (cell_row<K, EIX, 1>(o, p) + cell_row<K, EIX, 0>(o, q));
           if (bvec) v += beta * bvec[row + gx];
           y[row + gx] = v;
         }

@@ -31,11 +31,23 @@ struct SweepCfg {
   static_assert(SMEM <= 227 * 1024, "sweep kernel shared memory exceeds the per-CTA limit");
 };
 
-// cells per tile edge of the operator kernel
-constexpr int apply_bc(int dim, int k) {
-  return dim == 3 ? (k == 1 ? 8 : k == 2 ? 4 : k <= 4 ? 2 : 1)
-                  : (k == 1 ? 16 : k == 2 ? 8 : k <= 4 ? 4 : 2);
-}
+// Tile of the operator kernel (cells per direction x, y, z) and its threads.
+// A tile recomputes a halo of K + 1 nodes below it in each direction, so
+// flat tiles (large in x and y, one cell in z) do the least redundant work;
+// the FP64 kernel is bound by the FP64 pipe and takes them (measured on
+// GB300, 3D: k = 3 -34 %, k = 4 -37 %, k = 7 -39 % against cubes), the FP32
+// one keeps cubes (faster there), as do small degrees where cubes won.
+template <int DIM, int K>
+struct ApplyCfg {
+  static constexpr bool F64 = sizeof(T) == 8;
+  static constexpr int BC = DIM == 3 ? (K == 1 ? 8 : K == 2 ? 4 : K <= 4 ? 2 : 1)
+                                     : (K == 1 ? 16 : K == 2 ? 8 : K <= 4 ? 4 : 2);
+  static constexpr bool FLAT = F64 && DIM == 3 && K >= 3 && K <= 7;
+  static constexpr int BX = FLAT ? (K == 3 ? 8 : K == 4 ? 8 : K == 7 ? 4 : 2) : BC;
+  static constexpr int BY = FLAT ? (K == 3 ? 8 : K == 4 ? 4 : 2) : BC;
+  static constexpr int BZ = FLAT ? 1 : BC;
+  static constexpr int NT = FLAT ? 256 : kApplyThreads;
+};
 
 static int sm_count() {
   static int sms = 0;
@@ -181,22 +193,29 @@ static int table_impl(const PatchLaunch* pls, T* const* us, const T* const* bs, 
   return GMG_OK;
 }
 
-template <int DIM, int K>
-static int apply_impl(const ApplyLaunch& al, const T* x, T* y, const T* bvec, cudaStream_t s) {
-  constexpr int BC = apply_bc(DIM, K);
-  using D = ApplyDims<DIM, K, BC>;
-  auto kern = apply_kernel<DIM, K, BC, kApplyThreads>;
+template <int DIM, int K, int BX, int BY, int BZ, int NT>
+static int apply_cfg(const ApplyLaunch& al, const T* x, T* y, const T* bvec, cudaStream_t s) {
+  using D = ApplyDims<DIM, K, BX, BY, BZ>;
+  auto kern = apply_kernel<DIM, K, BX, BY, BZ, NT>;
   static bool ready = false;  // attribute set once (also keeps graph capture free of it)
   if (!ready) {
     if (prepare(kern, D::SMEM_BYTES) != GMG_OK) return GMG_ERR_CUDA;
     ready = true;
   }
-  long long tiles = (al.g.n + BC - 1) / BC;
-  long long ntile = DIM == 3 ? tiles * tiles * tiles : tiles * tiles;
+  const long long n = al.g.n;
+  const long long ntile = ((n + BX - 1) / BX) * ((n + BY - 1) / BY) * (DIM == 3 ? (n + BZ - 1) / BZ : 1);
   int grid = (int)std::min<long long>(ntile, 1 << 30);
-  kern<<<grid, kApplyThreads, D::SMEM_BYTES, s>>>(x, y, bvec, al);
+  kern<<<grid, NT, D::SMEM_BYTES, s>>>(x, y, bvec, al);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+}
+
+template <int DIM, int K>
+static int apply_impl(const ApplyLaunch& al, const T* x, T* y, const T* bvec, cudaStream_t s) {
+  using Cfg = ApplyCfg<DIM, K>;
+  static_assert(ApplyDims<DIM, K, Cfg::BX, Cfg::BY, Cfg::BZ>::SMEM_BYTES <= 227 * 1024,
+                "operator tile exceeds the shared memory of a CTA");
+  return apply_cfg<DIM, K, Cfg::BX, Cfg::BY, Cfg::BZ, Cfg::NT>(al, x, y, bvec, s);
 }
 
 #define GMG_DISPATCH(FN, DIMV, KV, ...)                                  \
