@@ -33,20 +33,20 @@ struct SweepCfg {
 
 // Tile of the operator kernel (cells per direction x, y, z) and its threads.
 // A tile recomputes a halo of K + 1 nodes below it in each direction, so
-// flat tiles (large in x and y, one cell in z) do the least redundant work;
-// the FP64 kernel is bound by the FP64 pipe and takes them (measured on
-// GB300, 3D: k = 3 -34 %, k = 4 -37 %, k = 7 -39 % against cubes), the FP32
-// one keeps cubes (faster there), as do small degrees where cubes won.
+// flat tiles (large in x and y, one cell in z) do less redundant work; the
+// shapes below were measured on GB300 (3D, against cubes): FP64 k = 3 -34 %,
+// k = 4 -37 %, k = 7 -39 %; FP32 k = 3 -49 %, k = 7 -50 %; FP32 k = 4 and the
+// small degrees are fastest with cubes.
 template <int DIM, int K>
 struct ApplyCfg {
   static constexpr bool F64 = sizeof(T) == 8;
   static constexpr int BC = DIM == 3 ? (K == 1 ? 8 : K == 2 ? 4 : K <= 4 ? 2 : 1)
                                      : (K == 1 ? 16 : K == 2 ? 8 : K <= 4 ? 4 : 2);
-  static constexpr bool FLAT = F64 && DIM == 3 && K >= 3 && K <= 7;
-  static constexpr int BX = FLAT ? (K == 3 ? 8 : K == 4 ? 8 : K == 7 ? 4 : 2) : BC;
-  static constexpr int BY = FLAT ? (K == 3 ? 8 : K == 4 ? 4 : 2) : BC;
+  static constexpr bool FLAT = DIM == 3 && (F64 ? (K >= 3 && K <= 7) : (K == 3 || K == 7));
+  static constexpr int BX = !FLAT ? BC : K == 3 ? (F64 ? 8 : 4) : K == 4 ? 8 : K == 7 ? 4 : 2;
+  static constexpr int BY = !FLAT ? BC : K == 3 ? (F64 ? 8 : 4) : K == 4 ? 4 : 2;
   static constexpr int BZ = FLAT ? 1 : BC;
-  static constexpr int NT = FLAT ? 256 : kApplyThreads;
+  static constexpr int NT = FLAT && !(K == 3 && !F64) ? 256 : kApplyThreads;
 };
 
 static int sm_count() {
