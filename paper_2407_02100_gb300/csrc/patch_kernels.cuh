@@ -73,6 +73,19 @@ __device__ __forceinline__ T patch_row(int i, const T (&x)[2 * K + 1], T acc = T
   return acc;
 }
 
+// The same row restricted to the two end columns 0 and 2K of the closure
+// (a closure line whose other entries are taken as zero).
+template <int K, int KIND>
+__device__ __forceinline__ T patch_row_ends(int i, T x0, T xc) {
+  constexpr int C = 2 * K + 1;
+  T acc = T(0);
+  if (band_lo(i + 1, K) == 0)
+    acc = (KIND == 0 ? c_Mp[off_patch(K) + i * C] : c_Kp[off_patch(K) + i * C]) * x0;
+  if (band_hi(i + 1, K) == 2 * K)
+    acc = fma(KIND == 0 ? c_Mp[off_patch(K) + i * C + C - 1] : c_Kp[off_patch(K) + i * C + C - 1], xc, acc);
+  return acc;
+}
+
 // FD transforms of one line of M = 2K-1 values held in registers, using the
 // mirror symmetry of the eigenvectors: modes 0..K-1 are even
 // (T[M-1-j][i] = T[j][i]), modes K..M-1 odd (T[M-1-j][i] = -T[j][i]).
@@ -203,6 +216,14 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
                                                           const __grid_constant__ TmaMaps<ME> maps,
                                                           int* __restrict__ err) {
   constexpr bool TMA = ME > 0;
+  // FP64, 3D: the local solver is exact (fast diagonalisation of the
+  // constant-coefficient patch), so the updated interior A_j^{-1} (b_j -
+  // bar A_j bar u_j) + u_j equals A_j^{-1} (b_j - bar A_j bar u_j^0), bar u_j^0
+  // the closure with its interior set to zero: the residual is evaluated
+  // with a zero interior and the scatter writes omega d + (1 - omega) u_j.
+  // (FP32 keeps the correction form: recomputing the interior would cost
+  // a factor cond(A_j) in single precision.)
+  constexpr bool EXACT = sizeof(T) == 8 && DIM == 3;
   using Z = SweepSmem<DIM, K, TMA>;
   constexpr int C = Z::C, M = Z::M, XU = Z::XU, XB = Z::XB;
   constexpr int LINES = DIM == 3 ? M * M : M;  // interior lines per axis
@@ -357,17 +378,58 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
       // solve only: nothing to evaluate, the buffer holds the residual
     } else if (DIM == 3) {
       // ---- stage z: P = Mp_z u, Q = Kp_z u   (dims x:C, y:C, z:M, in WB) ----
-      for (int idx = threadIdx.x; idx < nvalid * C * C; idx += NT) {
-        const int q = idx / (C * C), l = idx % (C * C);
-        const T* U = IN + q * Z::IN + ushift(cur, q) + uo(l % C, l / C, 0);
-        T* B = WB + q * Z::WB;
-        T x[C];
+      if constexpr (EXACT) {
+        // the patch interior is taken as zero (see the scatter): a line with
+        // (x, y) inside the patch has only its two end values left.  Lines
+        // are enumerated interior ones first, patches interleaved, so that a
+        // warp runs one kind of line.
+        constexpr int CI = C - 2;
+        for (int idx = threadIdx.x; idx < nvalid * C * C; idx += NT) {
+          const int q = idx % nvalid, lp = idx / nvalid;
+          int x, y;
+          if (lp < CI * CI) {
+            x = 1 + lp % CI;
+            y = 1 + lp / CI;
+          } else {
+            const int e = lp - CI * CI;
+            if (e < C) { x = e; y = 0; }
+            else if (e < 2 * C) { x = e - C; y = C - 1; }
+            else { x = ((e - 2 * C) & 1) ? C - 1 : 0; y = 1 + (e - 2 * C) / 2; }
+          }
+          const int l = x + C * y;
+          const T* U = IN + q * Z::IN + ushift(cur, q) + uo(x, y, 0);
+          T* B = WB + q * Z::WB;
+          if (lp < CI * CI) {
+            const T u0 = U[0], uc = U[(C - 1) * C * XU];
 #pragma unroll
-        for (int j = 0; j < C; ++j) x[j] = U[j * C * XU];
+            for (int i = 0; i < M; ++i) {
+              B[l + i * C * C] = patch_row_ends<K, 0>(i, u0, uc);
+              B[C * C * M + l + i * C * C] = patch_row_ends<K, 1>(i, u0, uc);
+            }
+          } else {
+            T xv[C];
 #pragma unroll
-        for (int i = 0; i < M; ++i) {
-          B[l + i * C * C] = patch_row<K, 0>(i, x);
-          B[C * C * M + l + i * C * C] = patch_row<K, 1>(i, x);
+            for (int j = 0; j < C; ++j) xv[j] = U[j * C * XU];
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+              B[l + i * C * C] = patch_row<K, 0>(i, xv);
+              B[C * C * M + l + i * C * C] = patch_row<K, 1>(i, xv);
+            }
+          }
+        }
+      } else {
+        for (int idx = threadIdx.x; idx < nvalid * C * C; idx += NT) {
+          const int q = idx / (C * C), l = idx % (C * C);
+          const T* U = IN + q * Z::IN + ushift(cur, q) + uo(l % C, l / C, 0);
+          T* B = WB + q * Z::WB;
+          T x[C];
+#pragma unroll
+          for (int j = 0; j < C; ++j) x[j] = U[j * C * XU];
+#pragma unroll
+          for (int i = 0; i < M; ++i) {
+            B[l + i * C * C] = patch_row<K, 0>(i, x);
+            B[C * C * M + l + i * C * C] = patch_row<K, 1>(i, x);
+          }
         }
       }
       __syncthreads();
@@ -492,7 +554,8 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
       const long long row = s_origin[cur][q] + 1 + py * (l % M + 1) + (DIM == 3 ? pz * (l / M + 1) : 0);
 #pragma unroll
       for (int i = 0; i < M; ++i)
-        u[row + i] = fma(om, d[i], mode == 0 ? U[i] : u[row + i]);
+        u[row + i] = EXACT && DIM == 3 && mode == 0 ? fma(om, d[i], (T(1) - om) * U[i])
+                                                    : fma(om, d[i], mode == 0 ? U[i] : u[row + i]);
     }
     if (TMA) async::fence_proxy_async();  // reads of the buffers before the next TMA writes
     __syncthreads();  // buffers and origins are refilled / reused next iteration
