@@ -41,9 +41,9 @@ BYTES_PER_NODE = 24
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 # DRAM bytes of one average colour launch of the FP64 sweep kernel at this
-# workload, from an ncu capture of the current kernel (282.8 MB for the
+# workload, from an ncu capture of the current kernel (283.1 MB for the
 # 29,791-patch colour 0, scaled by patches to the 31,256-patch average)
-TRAFFIC_PER_LAUNCH = 282.805760e6 * 31256.0 / 29791.0
+TRAFFIC_PER_LAUNCH = 283.131136e6 * 31256.0 / 29791.0
 CPU_SAMPLE = dict(dim=3, degree=4, n_cells=8, n_levels=3)
 WORKLOAD = ("3D Poisson Q4, 64^3 cells, FP64 GMG(V(1,1), 8-colour vertex-patch smoother) "
             "preconditioned CG to 1e-10")
@@ -374,8 +374,8 @@ def run_ours(args):
                                        "colour launch (29,791 patches) scaled to the average launch "
                                        "(31,256 patches)",
                      "algorithmic_bytes_per_launch": BYTES_PER_NODE * nodes / 8,
-                     "fp64_pipe_active_ncu": 0.814,
-                     "kernel": "patch_colour_kernel<3,4,256,4,1> (FP64), one launch per colour",
+                     "fp64_pipe_active_ncu": 0.817,
+                     "kernel": "patch_colour_kernel<3,4,256,4,1,1> (FP64, TMA gather), one launch per colour",
                      "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz",
                      "note": "achieved counts the method's operation count (98,812 flop per patch); "
                              "the kernel executes fewer (banded two-cell matrices, even/odd FD), "
