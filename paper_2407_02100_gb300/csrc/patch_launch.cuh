@@ -61,11 +61,11 @@ static int sm_count() {
 }
 
 template <typename KernelT>
+// opt the kernel in to its dynamic shared memory (the 48 KB default covers
+// static plus dynamic memory, so the attribute is set whatever the size)
 static int prepare(KernelT kern, int smem) {
-  if (smem > 48 * 1024) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-      return GMG_ERR_CUDA;
-  }
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return GMG_ERR_CUDA;
   return GMG_OK;
 }
 
