@@ -226,3 +226,34 @@ def test_full_size_colour_step_on_sampled_patches(gmg, prec, tol):
     touched = np.zeros(m.n_nodes, dtype=bool)
     touched[m.interior_index(V).ravel()] = True
     assert np.array_equal(got[~touched], u0[~touched])
+
+
+@pytest.mark.parametrize("dim,k,ns,prec", [(2, 2, (8, 16, 32), 0), (2, 3, (4, 8, 16), 1),
+                                           (3, 2, (4, 8, 16), 0), (3, 4, (2, 4, 8), 1)])
+def test_manufactured_solution_solved_on_the_gpu_converges(gmg, dim, k, ns, prec):
+    """-Laplace u = f with u = prod sin(pi x_a) (App. A.2's test problem):
+    the GPU GMG-PCG solution (FP64, or FP32 V-cycle in FP64 CG) of the
+    discrete problem has an L2 error falling at O(h^(k+1)) and matches the
+    oracle's direct solution of the same system."""
+    import torch
+    from oracle import problem
+    u_exact, f = problem.sine_solution(dim)
+    errs = []
+    for n in ns:
+        m = Mesh(dim, k, n)
+        b = problem.load_vector(m, f)
+        P = gmg.Problem(dim, k, n, precision=prec)
+        u = P.zeros(dtype=torch.float64)
+        _, st = gmg.cg_gmg_solve(P.h, u, P.to_device(b, dtype=torch.float64), 1e-12, 100)
+        assert st.converged
+        got = P.from_device(u)
+        errs.append(problem.l2_error(m, got, u_exact))
+        if n == ns[0]:
+            A = m.assemble()
+            inner = m.interior_nodes()
+            ref = np.zeros_like(b)
+            import scipy.sparse.linalg as spla
+            ref[inner] = spla.spsolve(A[inner][:, inner].tocsc(), b[inner])
+            close(got, ref, 1e-10, "direct solution")
+    rates = [np.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert min(rates) > k + 1 - 0.3, (errs, rates)
