@@ -19,38 +19,36 @@ inline int grid_for(long long n, int threads) {
 }
 
 // out[o + out_off] (+)= sum_w coef[(o_ax % R) W + w] in[(o_ax / R) S + off + w]
-// with one thread per output element (x index fastest, so that loads and
-// stores along the contiguous axis coalesce).
-template <typename T>
+// with one thread per output element: threads along x (loads and stores
+// along the contiguous axis coalesce), blocks along y and z (grid-strided
+// beyond the grid limits), the contracted axis AX a template parameter.
+template <typename T, int AX>
 __global__ void axis_op_kernel(const T* __restrict__ in, T* __restrict__ out,
                                const T* __restrict__ coef, AxisOp op) {
-  const long long total = (long long)op.cnt[0] * op.cnt[1] * op.cnt[2];
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    int o[3];
-    o[0] = (int)(e % op.cnt[0]);
-    long long r = e / op.cnt[0];
-    o[1] = (int)(r % op.cnt[1]);
-    o[2] = (int)(r / op.cnt[1]);
-    long long ibase = 0, obase = 0;
+  const int o0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o0 >= op.cnt[0]) return;
+  const long long sa = op.in_stride[AX];
+  const int lim = op.in_dim[AX];
+  for (int o2 = blockIdx.z; o2 < op.cnt[2]; o2 += gridDim.z)
+    for (int o1 = blockIdx.y; o1 < op.cnt[1]; o1 += gridDim.y) {
+      const int o[3] = {o0, o1, o2};
+      long long ibase = 0, obase = 0;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      obase += (long long)(o[a] + op.out_off[a]) * op.out_stride[a];
-      if (a != op.axis) ibase += (long long)(o[a] + op.in_off[a]) * op.in_stride[a];
+      for (int a = 0; a < 3; ++a) {
+        obase += (long long)(o[a] + op.out_off[a]) * op.out_stride[a];
+        if (a != AX) ibase += (long long)(o[a] + op.in_off[a]) * op.in_stride[a];
+      }
+      const int oa = o[AX] + op.shift;
+      const int start = (oa / op.R) * op.S + op.off;
+      const T* __restrict__ c = coef + (oa % op.R) * op.W;
+      T acc = T(0);
+      for (int w = 0; w < op.W; ++w) {
+        const int i = start + w;
+        if (i >= 0 && i < lim) acc += __ldg(c + w) * in[ibase + i * sa];
+      }
+      if (op.accumulate) out[obase] += acc;
+      else out[obase] = acc;
     }
-    const int oa = o[op.axis] + op.shift;
-    const int start = (oa / op.R) * op.S + op.off;
-    const T* c = coef + (oa % op.R) * op.W;
-    const long long sa = op.in_stride[op.axis];
-    const int lim = op.in_dim[op.axis];
-    T acc = T(0);
-    for (int w = 0; w < op.W; ++w) {
-      int i = start + w;
-      if (i >= 0 && i < lim) acc += c[w] * in[ibase + i * sa];
-    }
-    if (op.accumulate) out[obase] += acc;
-    else out[obase] = acc;
-  }
 }
 
 template <typename T>
@@ -212,9 +210,14 @@ inline int status(int launches = 1) {
 
 template <typename T>
 int launch_axis_op(const AxisOp& op, const T* in, T* out, const T* coef, cudaStream_t s) {
-  long long total = (long long)op.cnt[0] * op.cnt[1] * op.cnt[2];
-  if (total <= 0) return GMG_OK;
-  axis_op_kernel<T><<<grid_for(total, kThreads), kThreads, 0, s>>>(in, out, coef, op);
+  if ((long long)op.cnt[0] * op.cnt[1] * op.cnt[2] <= 0) return GMG_OK;
+  const int tx = op.cnt[0] >= 256 ? 256 : op.cnt[0] >= 128 ? 128 : op.cnt[0] >= 64 ? 64 : 32;
+  const dim3 grid((op.cnt[0] + tx - 1) / tx, std::min(op.cnt[1], 65535), std::min(op.cnt[2], 65535));
+  switch (op.axis) {
+    case 0: axis_op_kernel<T, 0><<<grid, tx, 0, s>>>(in, out, coef, op); break;
+    case 1: axis_op_kernel<T, 1><<<grid, tx, 0, s>>>(in, out, coef, op); break;
+    default: axis_op_kernel<T, 2><<<grid, tx, 0, s>>>(in, out, coef, op); break;
+  }
   return status();
 }
 template int launch_axis_op<double>(const AxisOp&, const double*, double*, const double*, cudaStream_t);
