@@ -28,6 +28,8 @@ def main():
     ap.add_argument("--variant", choices=["combined", "separated", "batched"], default="combined",
                     help="Algorithm 4, 3 or 5 of the paper")
     ap.add_argument("--batch", type=int, default=32768, help="n_B of Algorithm 5")
+    ap.add_argument("--no-apply", action="store_true",
+                    help="time the sweep only (for captures of the sweep's kernels alone)")
     ap.add_argument("--slab", type=int, default=0,
                     help="skewed-slab width in vertex rows (0: one launch per colour, -1: fit L2)")
     a = ap.parse_args()
@@ -55,7 +57,7 @@ def main():
     variant = {"combined": gmg.GMG_SWEEP_COMBINED, "separated": gmg.GMG_SWEEP_SEPARATED,
                "batched": gmg.GMG_SWEEP_BATCHED}[a.variant]
     t_sweep = timed(lambda: gmg.gmg_smooth_variant(P.h, 0, u, b, variant, a.batch, False), a.sweeps)
-    t_apply = timed(lambda: gmg.gmg_apply_operator(P.h, 0, u, y), a.sweeps)
+    t_apply = float("nan") if a.no_apply else timed(lambda: gmg.gmg_apply_operator(P.h, 0, u, y), a.sweeps)
     nodes = (a.n * a.degree + 1) ** a.dim
     print(json.dumps({"dim": a.dim, "degree": a.degree, "n_cells": a.n, "precision": a.precision,
                       "variant": a.variant, "batch": a.batch if a.variant == "batched" else None,
