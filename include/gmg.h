@@ -358,6 +358,31 @@ int gmg_set_slab_width(gmg_problem* p, int width);
  * negative status. */
 int gmg_slab_width(const gmg_problem* p, int level);
 
+/* ---- Shared-face form of the FP64 3D sweep -------------------------------
+ * Constant-coefficient FP64 problems in 3D of degree >= 3 evaluate the local
+ * residual of a whole-colour sweep (Algorithm 4) from the closure boundary
+ * only: the local solver is exact (App. A.3), so the new interior is
+ * A_j^{-1}(b_j - bar A_j bar u_j^0) with the patch interior of bar u_j^0 set
+ * to zero, and bar A_j bar u_j^0 is a sum over the six closure faces of
+ * one-dimensional columns of the two-cell matrices times two-dimensional
+ * sum-factorised face terms (eq. "main:4" restricted to the boundary).  A
+ * face plane between two same-colour patches has the same terms in both, so
+ * each colour launch first evaluates every face once (face kernel) and the
+ * patch kernel reads them.  Same method and colour order; results agree
+ * with the closure form up to rounding.  The face buffer (allocated by
+ * gmg_create: 12 (2k-1)^2 doubles per patch of the finest level's largest
+ * colour, about 0.6x a level vector at k = 4) is shared by all levels; if it
+ * cannot be allocated the closure form is used.  Algorithm 3 and 5, slab
+ * schedules, batches and single-precision problems always use the closure
+ * form.
+ * gmg_set_shared_faces: enable (default) or disable the form; returns
+ *   GMG_ERR_INVALID_ARG for a null problem.
+ * gmg_shared_faces: 1 if whole-colour FP64 3D sweeps of the problem use the
+ *   form (enabled and the buffer allocated), 0 if not, GMG_ERR_INVALID_ARG
+ *   for a null problem. */
+int gmg_set_shared_faces(gmg_problem* p, int enable);
+int gmg_shared_faces(const gmg_problem* p);
+
 /* ---- Tensor-core sweep (GMG_FP32_TC) and bounded device waits ----------
  * Every patch of one colour is processed as in gmg_smooth (Algorithm 4,
  * local_update of Sec. 3.1: gather, local residual by sum factorisation,

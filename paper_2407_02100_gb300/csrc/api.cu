@@ -126,8 +126,14 @@ PatchLaunch colour_launch(const Level& L, int colour, double omega) {
 
 int launch_colour(gmg_problem* p, const PatchLaunch& pl, void* u, const void* b) {
   if (pl.n_patches == 0) return GMG_OK;
-  if (p->esize == 8)
+  if (p->esize == 8) {
+    if (p->faces && p->shared_faces) {
+      const int st = launch_patch_faces(pl, (double*)u, (const double*)b, (const double*)p->dinv,
+                                        (double*)p->faces, p->stream);
+      if (st != GMG_ERR_UNSUPPORTED) return st;
+    }
     return launch_patch_colour<double>(pl, (double*)u, (const double*)b, (const double*)p->dinv, p->stream);
+  }
   const int pr = p->desc.precision;
   if ((pr == GMG_FP32_TC || pr == GMG_FP32_TF32) && pl.mode == 0 && tc_supported(pl.g.dim, pl.g.k))
     return launch_patch_tc(pl, (float*)u, (const float*)b, (const float*)p->dinv, pr == GMG_FP32_TC, p->stream);
@@ -595,6 +601,14 @@ int gmg::detail::create_problem(const gmg_desc* d, gmg_problem* p, const CreateO
     dinv[t] = 1.0 / s;
   }
   CHECK(upload_table(p, &p->dinv, dinv));
+  // face buffer of the shared-face FP64 sweep: the largest colour of the
+  // finest level; without memory for it the closure form is used
+  if (p->esize == 8 && dim == 3 && k >= 3 && !opt.no_faces) {
+    long long fe = 0;
+    for (int c = 0; c < (1 << dim); ++c)
+      fe = std::max(fe, face_buffer_elems(colour_launch(p->levels[L - 1], c, d->damping)));
+    if (fe > 0 && dalloc(p, &p->faces, fe * 8) != GMG_OK) p->faces = nullptr;
+  }
   // transfer tables
   std::vector<double> P1;
   prolongation_cell_1d(k, P1);  // (2k+1) x (k+1)
@@ -825,6 +839,18 @@ int gmg_set_local_solver(gmg_problem* p, int solver) {
     return GMG_OK;
   }
   return GMG_ERR_INVALID_ARG;
+}
+
+int gmg_set_shared_faces(gmg_problem* p, int enable) {
+  if (!p) return GMG_ERR_INVALID_ARG;
+  drop_cg_graph(p);
+  p->shared_faces = enable != 0;
+  return GMG_OK;
+}
+
+int gmg_shared_faces(const gmg_problem* p) {
+  if (!p) return GMG_ERR_INVALID_ARG;
+  return p->shared_faces && p->faces ? 1 : 0;
 }
 
 int gmg_set_slab_width(gmg_problem* p, int width) {

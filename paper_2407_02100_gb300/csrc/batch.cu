@@ -291,6 +291,7 @@ int gmg_batch_create(const gmg_desc* desc, int n_problems, const int* n_cells, g
     opt.finest_b = at(B->fb, B->off[i], B->esize);
     opt.finest_r = at(B->fr, B->off[i], B->esize);
     opt.no_cg = true;
+    opt.no_faces = true;
     if ((st = create_problem(&d, p, opt))) return fail(st);
     B->max_depth = std::max(B->max_depth, (int)p->levels.size());
   }

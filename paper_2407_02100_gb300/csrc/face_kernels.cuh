@@ -1,0 +1,525 @@
+// Shared-face form of the FP64 3D patch sweep (combined colourised smoother,
+// Algorithm 4, constant coefficient, degrees 3..8).  Included by patch_f64.cu
+// after patch_kernels.cuh and patch_launch.cuh (T = double).
+//
+// The local solver is exact, so the updated interior of patch j is
+// A_j^{-1} (b_j - bar A_j bar u_j^0), bar u_j^0 its closure with the interior
+// set to zero (App. A.3 with eqs. "main:4", "gather", "scatter").  The
+// product bar A_j bar u_j^0 then involves only the closure boundary: its
+// six faces.  With the two-cell 1D matrices M, K (interior rows, closure
+// columns; M_I, K_I their interior columns) and the patch operator
+// K (x) M (x) M + M (x) K (x) M + M (x) M (x) K (x fastest, axes x, y, z):
+//   x face at closure x = f (all y, z; data v):
+//     F1 = (M_y (x) M_z) v,  F2 = (K_y (x) M_z + M_y (x) K_z) v,
+//     contribution K_x[:, f] (x) F1 + M_x[:, f] (x) F2;
+//   y face at y = f (x interior, all z; data w):
+//     G1 = (K_I,x (x) M_z + M_I,x (x) K_z) w,  G2 = (M_I,x (x) M_z) w,
+//     contribution M_y[:, f] (x) G1 + K_y[:, f] (x) G2;
+//   z face at z = f (x, y interior; data s):
+//     H1 = (K_I,x (x) M_I,y + M_I,x (x) K_I,y) s,  H2 = (M_I,x (x) M_I,y) s,
+//     contribution M_z[:, f] (x) H1 + K_z[:, f] (x) H2.
+// F, G, H depend only on the face's node values and on its extent, and the
+// face between two same-colour neighbours has the same extent in both
+// patches: each face plane is evaluated once per colour (face kernel) and
+// read by the two patches that share it (patch kernel).  Same-colour
+// patches never write each other's closure, so the faces of a colour stay
+// valid while its patches are updated.
+#pragma once
+#include "async.cuh"
+
+namespace gmg {
+namespace GMG_NS {
+
+// Faces of one colour.  Patch (i_x, i_y, i_z) of the colour owns
+//   x faces fx = i_x, i_x + 1 of X[(i_z c_y + i_y)(c_x + 1) + fx],
+//   y faces fy = i_y, i_y + 1 of Y[(i_z (c_y + 1) + fy) c_x + i_x],
+//   z faces fz = i_z, i_z + 1 of Z[(fz c_y + i_y) c_x + i_x].
+// Each face holds two M x M fields: x faces F1, F2 as [l][j] (l the z row,
+// j the y row), y faces G1, G2 as [l][i], z faces H1, H2 as [j][i]
+// (i the x row); the families start at foff[0..2] elements.
+struct FaceGeom {
+  long long py, pz;
+  int first[3], count[3];
+  long long nf[3];
+  long long foff[3];
+};
+
+__host__ __device__ constexpr int face_fields(int k) { return 2 * (2 * k - 1) * (2 * k - 1); }
+
+// acc + sum over the interior columns of row i of M_p (KIND 0) or K_p
+// (KIND 1), x[a] the value at interior column a (closure column a + 1)
+template <int K, int KIND>
+__device__ __forceinline__ T patch_row_int(int i, const T (&x)[2 * K - 1], T acc = T(0)) {
+  constexpr int C = 2 * K + 1, M = 2 * K - 1;
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    if (a + 1 >= band_lo(i + 1, K) && a + 1 <= band_hi(i + 1, K)) {
+      const T e = KIND == 0 ? c_Mp[off_patch(K) + i * C + a + 1] : c_Kp[off_patch(K) + i * C + a + 1];
+      acc = fma(e, x[a], acc);
+    }
+  }
+  return acc;
+}
+
+// element offset of the first node of face f of family fam (0 x, 1 y, 2 z):
+// the face planes of patch (i_x, i_y, i_z) sit at its closure origin (index
+// i) and at the next patch's (index i + 1); in-plane the data start at the
+// closure origin (axes the face spans completely) or one node inside it
+// (interior rows)
+template <int K>
+__device__ __forceinline__ long long face_origin(const FaceGeom& fg, int fam, long long f) {
+  const int cx = fg.count[0], cy = fg.count[1];
+  long long ix, iy, iz;
+  if (fam == 0) {
+    ix = f % (cx + 1);
+    const long long r = f / (cx + 1);
+    iy = r % cy;
+    iz = r / cy;
+  } else if (fam == 1) {
+    ix = f % cx;
+    const long long r = f / cx;
+    iy = r % (cy + 1);
+    iz = r / (cy + 1);
+  } else {
+    ix = f % cx;
+    const long long r = f / cx;
+    iy = r % cy;
+    iz = r / cy;
+  }
+  const long long X = (fg.first[0] + 2 * ix - 1) * K + (fam == 0 ? 0 : 1);
+  const long long Y = (fg.first[1] + 2 * iy - 1) * K + (fam == 2 ? 1 : 0);
+  const long long Z = (fg.first[2] + 2 * iz - 1) * K;
+  return X + fg.py * Y + fg.pz * Z;
+}
+
+// faces per CTA of the face kernel: enough first-stage lines for NT threads
+template <int K, int NT>
+struct FaceCfg {
+  static constexpr int C = 2 * K + 1, M = 2 * K - 1;
+  static constexpr int FX = NT / C > 0 ? NT / C : 1, FYZ = NT / M > 0 ? NT / M : 1;
+  // per face: input, then the first-stage P and Q
+  static constexpr int SX = C * C + 2 * C * M, SY = M * C + 2 * M * M, SZ = M * M + 2 * M * M;
+  static constexpr int SMEM = cmax(FX * SX, cmax(FYZ * SY, FYZ * SZ)) * (int)sizeof(T);
+};
+
+// Face kernel: CTAs [0, bx) evaluate x faces, [bx, bx + by) y faces, the rest
+// z faces, FX (FYZ) faces per CTA.  First stage: contract z (x and y faces,
+// all closure rows of the two-cell matrices) or y (z faces, interior
+// columns); second stage: contract the remaining in-plane axis.
+template <int K, int NT>
+__global__ void __launch_bounds__(NT) face_kernel(const T* __restrict__ u, T* __restrict__ faces,
+                                                  const __grid_constant__ FaceGeom fg, int bx, int by) {
+  using F = FaceCfg<K, NT>;
+  constexpr int C = F::C, M = F::M, FS = face_fields(K);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* const S = reinterpret_cast<T*>(smem_raw);
+  int fam, blk;
+  if ((int)blockIdx.x < bx) { fam = 0; blk = blockIdx.x; }
+  else if ((int)blockIdx.x < bx + by) { fam = 1; blk = blockIdx.x - bx; }
+  else { fam = 2; blk = blockIdx.x - bx - by; }
+  const int per = fam == 0 ? F::FX : F::FYZ;
+  const long long f0 = (long long)blk * per;
+  const int nq = (int)min((long long)per, fg.nf[fam] - f0);
+  T* const out = faces + fg.foff[fam] + f0 * FS;
+  if (fam == 0) {
+    // ---- x faces: v[y][z] (C x C); P, Q[y][l] = (M_z, K_z) v[y][:] ----
+    T* V = S;
+    T* P = S + F::FX * C * C;
+    T* Q = P + F::FX * C * M;
+    for (int t = threadIdx.x; t < nq * C * C; t += NT) {
+      const int q = t % nq, e = t / nq, y = e % C, z = e / C;  // faces fastest: nearby x planes
+      V[q * C * C + y * C + z] = u[face_origin<K>(fg, 0, f0 + q) + fg.py * y + fg.pz * z];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nq * C; t += NT) {
+      const int q = t / C, y = t % C;
+      T v[C];
+#pragma unroll
+      for (int z = 0; z < C; ++z) v[z] = V[q * C * C + y * C + z];
+#pragma unroll
+      for (int l = 0; l < M; ++l) {
+        P[(q * C + y) * M + l] = patch_row<K, 0>(l, v);
+        Q[(q * C + y) * M + l] = patch_row<K, 1>(l, v);
+      }
+    }
+    __syncthreads();
+    // F1[l][j] = (M_y P)[j][l], F2[l][j] = (K_y P + M_y Q)[j][l]
+    for (int t = threadIdx.x; t < nq * M; t += NT) {
+      const int q = t / M, l = t % M;
+      T p[C], r[C];
+#pragma unroll
+      for (int y = 0; y < C; ++y) {
+        p[y] = P[(q * C + y) * M + l];
+        r[y] = Q[(q * C + y) * M + l];
+      }
+      T* o = out + (long long)q * FS + l * M;
+#pragma unroll
+      for (int j = 0; j < M; ++j) {
+        o[j] = patch_row<K, 0>(j, p);
+        o[M * M + j] = patch_row<K, 0>(j, r, patch_row<K, 1>(j, p));
+      }
+    }
+    return;
+  }
+  T* P = S + F::FYZ * (fam == 1 ? M * C : M * M);
+  T* Q = P + F::FYZ * M * M;
+  if (fam == 1) {
+    // ---- y faces: w[a][z] (a the interior x row); P, Q[a][l] = (M_z, K_z) w[a][:] ----
+    T* W = S;
+    for (int t = threadIdx.x; t < nq * M * C; t += NT) {
+      const int a = t % M, e = t / M, z = e % C, q = e / C;  // x fastest: contiguous rows
+      W[(q * M + a) * C + z] = u[face_origin<K>(fg, 1, f0 + q) + a + fg.pz * z];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nq * M; t += NT) {
+      const int q = t / M, a = t % M;
+      T v[C];
+#pragma unroll
+      for (int z = 0; z < C; ++z) v[z] = W[(q * M + a) * C + z];
+#pragma unroll
+      for (int l = 0; l < M; ++l) {
+        P[(q * M + a) * M + l] = patch_row<K, 0>(l, v);
+        Q[(q * M + a) * M + l] = patch_row<K, 1>(l, v);
+      }
+    }
+  } else {
+    // ---- z faces: s[a][b] (interior x row a, y row b); P, Q[a][j] = (M_I, K_I) s[a][:] ----
+    T* Sz = S;
+    for (int t = threadIdx.x; t < nq * M * M; t += NT) {
+      const int a = t % M, e = t / M, b = e % M, q = e / M;
+      Sz[(q * M + a) * M + b] = u[face_origin<K>(fg, 2, f0 + q) + a + fg.py * b];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nq * M; t += NT) {
+      const int q = t / M, a = t % M;
+      T v[M];
+#pragma unroll
+      for (int b = 0; b < M; ++b) v[b] = Sz[(q * M + a) * M + b];
+#pragma unroll
+      for (int j = 0; j < M; ++j) {
+        P[(q * M + a) * M + j] = patch_row_int<K, 0>(j, v);
+        Q[(q * M + a) * M + j] = patch_row_int<K, 1>(j, v);
+      }
+    }
+  }
+  __syncthreads();
+  // y faces: G1[l][i] = (K_I P + M_I Q)[i][l], G2[l][i] = (M_I P)[i][l];
+  // z faces: the same with l -> j (H1, H2)
+  for (int t = threadIdx.x; t < nq * M; t += NT) {
+    const int q = t / M, l = t % M;
+    T p[M], r[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      p[a] = P[(q * M + a) * M + l];
+      r[a] = Q[(q * M + a) * M + l];
+    }
+    T* o = out + (long long)q * FS + l * M;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      o[i] = patch_row_int<K, 0>(i, r, patch_row_int<K, 1>(i, p));
+      o[M * M + i] = patch_row_int<K, 0>(i, p);
+    }
+  }
+}
+
+// Shared-memory plan of the shared-face sweep, per patch (doubles):
+//   IN (NBUF copies): interior rows of b (TMA box rows of XB, as in the
+//       closure kernel), then the face blocks X0 X1 Y0 Y1 Z0 Z1 of the patch
+//       (two M x M fields each, copied by cp.async.bulk); 128-byte multiple
+//   WB: the FD work (M^3)
+template <int K>
+struct FaceSweepSmem {
+  static constexpr int C = 2 * K + 1, M = 2 * K - 1;
+  static constexpr int A = 16 / (int)sizeof(T);
+  static constexpr int XB = (C + A - 1 + A - 1) / A * A;
+  static constexpr int R128 = 128 / (int)sizeof(T);
+  static constexpr int NBIN = (M * M * XB + R128 - 1) / R128 * R128;
+  static constexpr int FS = face_fields(K);
+  static constexpr int IN = (NBIN + 6 * FS + R128 - 1) / R128 * R128;
+  static constexpr int WB = M * M * M;
+  static constexpr int per_patch(int nbuf) { return nbuf * IN + WB; }
+  static constexpr int BOX_B = M * M * XB * (int)sizeof(T);
+  static constexpr int FACE_BYTES = FS * (int)sizeof(T);
+};
+
+struct FaceSweepArgs {
+  T* u;
+  const T* faces;
+  const T* dinv;
+  int* err;
+  long long py, pz;
+  int first[3], count[3];
+  int n_patches, ngroups;
+  long long foff[3];
+  double sb, omega;
+};
+
+// One colour of the sweep, shared-face form.  Persistent CTAs walk groups of
+// PPC patches; lanes 0..PPC-1 of warp 0 issue, per patch, one TMA box of b
+// and six bulk copies of its face blocks, all completing on the slot's
+// mbarrier (bounded wait; an expired wait sets err and the kernel carries
+// on).  With NBUF = 2 the next group streams in while the current one is
+// computed.  Stages: r = sb b - (face contributions) per interior x line,
+// forward FD x | forward FD y | forward FD z, times the FD diagonal |
+// backward FD z | backward FD y | backward FD x + scatter
+// u = omega d + (1 - omega) u_old.
+template <int K, int NT, int PPC, int NBUF>
+__global__ void __launch_bounds__(NT) patch_face_kernel(const __grid_constant__ FaceSweepArgs fa,
+                                                        const __grid_constant__ CUtensorMap bmap) {
+  using Z = FaceSweepSmem<K>;
+  constexpr int C = Z::C, M = Z::M, XB = Z::XB, FS = Z::FS, LINES = M * M;
+  static_assert(PPC <= 32, "one lane of warp 0 issues the copies of one patch");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* const IN0 = reinterpret_cast<T*>(smem_raw + ((128 - (async::smem_u32(smem_raw) & 127)) & 127));
+  T* const WB = IN0 + NBUF * PPC * Z::IN;
+  __shared__ long long s_origin[2][PPC];
+  __shared__ int s_x[2][PPC][3];     // closure origin (lattice coordinates)
+  __shared__ long long s_face[2][PPC][6];  // element offsets of the six face blocks
+  __shared__ int s_nvalid[2];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  uint32_t phase = 0;
+  bool wait_ok = true;
+  const T om = (T)fa.omega, sb = (T)fa.sb;
+  const int cx = fa.count[0], cy = fa.count[1];
+  if (threadIdx.x == 0) {
+    async::mbar_init(&s_bar[0], 1);
+    async::mbar_init(&s_bar[1], 1);
+  }
+  __syncthreads();
+
+  auto set_origins = [&](int grp, int slot) {
+    const int nv = min(PPC, fa.n_patches - grp * PPC);
+    if (threadIdx.x == 0) s_nvalid[slot] = nv;
+    if (threadIdx.x < nv) {
+      const int pid = grp * PPC + threadIdx.x;
+      const int ix = pid % cx, rest = pid / cx, iy = rest % cy, iz = rest / cy;
+      const int o0 = (fa.first[0] + 2 * ix - 1) * K, o1 = (fa.first[1] + 2 * iy - 1) * K,
+                o2 = (fa.first[2] + 2 * iz - 1) * K;
+      s_origin[slot][threadIdx.x] = o0 + fa.py * o1 + fa.pz * o2;
+      s_x[slot][threadIdx.x][0] = o0;
+      s_x[slot][threadIdx.x][1] = o1;
+      s_x[slot][threadIdx.x][2] = o2;
+      const long long fxi = ((long long)iz * cy + iy) * (cx + 1) + ix;
+      const long long fyi = ((long long)iz * (cy + 1) + iy) * cx + ix;
+      const long long fzi = ((long long)iz * cy + iy) * cx + ix;
+      s_face[slot][threadIdx.x][0] = fa.foff[0] + fxi * FS;
+      s_face[slot][threadIdx.x][1] = fa.foff[0] + (fxi + 1) * FS;
+      s_face[slot][threadIdx.x][2] = fa.foff[1] + fyi * FS;
+      s_face[slot][threadIdx.x][3] = fa.foff[1] + (fyi + cx) * FS;
+      s_face[slot][threadIdx.x][4] = fa.foff[2] + fzi * FS;
+      s_face[slot][threadIdx.x][5] = fa.foff[2] + (fzi + (long long)cy * cx) * FS;
+    }
+  };
+  auto prefetch = [&](int slot) {
+    if (threadIdx.x >= 32) return;
+    const int nv = s_nvalid[slot];
+    if (threadIdx.x == 0)
+      async::mbar_arrive_expect_tx(&s_bar[slot], (uint32_t)(nv * (Z::BOX_B + 6 * Z::FACE_BYTES)));
+    __syncwarp();
+    const int q = threadIdx.x;
+    if (q < nv) {
+      T* dst = IN0 + (slot * PPC + q) * Z::IN;
+      const int x0 = s_x[slot][q][0], xa = x0 - x0 % Z::A;
+      async::tma_load_3d(dst, &bmap, xa, s_x[slot][q][1] + 1, s_x[slot][q][2] + 1, &s_bar[slot]);
+#pragma unroll
+      for (int f = 0; f < 6; ++f)
+        async::bulk_load(dst + Z::NBIN + f * FS, fa.faces + s_face[slot][q][f], Z::FACE_BYTES, &s_bar[slot]);
+    }
+  };
+  auto wait_gather = [&](int slot) {
+    if (wait_ok && !async::mbar_wait(&s_bar[slot], (phase >> slot) & 1u)) wait_ok = false;
+    phase ^= 1u << slot;
+  };
+
+  const int ngroups = fa.ngroups;
+  int grp = blockIdx.x;
+  if (NBUF == 2 && grp < ngroups) {
+    set_origins(grp, 0);
+    __syncthreads();
+    prefetch(0);
+  }
+  for (int it = 0; grp < ngroups; grp += gridDim.x, ++it) {
+    const int cur = NBUF == 2 ? (it & 1) : 0;
+    if (NBUF == 1) {
+      set_origins(grp, 0);
+      __syncthreads();
+      prefetch(0);
+      wait_gather(0);
+    } else if (grp + (int)gridDim.x < ngroups) {
+      set_origins(grp + gridDim.x, cur ^ 1);
+      __syncthreads();
+      prefetch(cur ^ 1);
+      wait_gather(cur);
+    } else {
+      wait_gather(cur);
+    }
+    __syncthreads();
+    const int nvalid = s_nvalid[cur];
+    const T* IN = IN0 + cur * PPC * Z::IN;
+
+    // ---- r = sb b - face contributions on interior x line (j, l), then the
+    // forward FD transform along x; result into WB ----
+    for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {
+      const int q = idx / LINES, ln = idx % LINES, j = ln % M, l = ln / M;
+      const T* P = IN + q * Z::IN;
+      const T* Bq = P + s_x[cur][q][0] % Z::A + 1 + (l * M + j) * XB;
+      const T* FX = P + Z::NBIN;          // X0, X1: F1[l][j], F2[l][j]
+      const T* FY = FX + 2 * FS + l * M;   // Y0, Y1: G1[l][.], G2[l][.]
+      const T* FZ = FX + 4 * FS + j * M;   // Z0, Z1: H1[j][.], H2[j][.]
+      const T f10 = FX[l * M + j], f20 = FX[M * M + l * M + j];
+      const T f11 = FX[FS + l * M + j], f21 = FX[FS + M * M + l * M + j];
+      // closure columns 0 and 2K of rows j (y faces) and l (z faces)
+      const int oj = off_patch(K) + j * C, ol = off_patch(K) + l * C;
+      const T my0 = c_Mp[oj], ky0 = c_Kp[oj], my1 = c_Mp[oj + C - 1], ky1 = c_Kp[oj + C - 1];
+      const T mz0 = c_Mp[ol], kz0 = c_Kp[ol], mz1 = c_Mp[ol + C - 1], kz1 = c_Kp[ol + C - 1];
+      T r[M], y[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        T acc = sb * Bq[i];
+        if (band_lo(i + 1, K) == 0)
+          acc = fma(-c_Kp[off_patch(K) + i * C], f10, fma(-c_Mp[off_patch(K) + i * C], f20, acc));
+        if (band_hi(i + 1, K) == 2 * K)
+          acc = fma(-c_Kp[off_patch(K) + i * C + C - 1], f11, fma(-c_Mp[off_patch(K) + i * C + C - 1], f21, acc));
+        acc = fma(-my0, FY[i], fma(-ky0, FY[M * M + i], acc));
+        acc = fma(-my1, FY[FS + i], fma(-ky1, FY[FS + M * M + i], acc));
+        acc = fma(-mz0, FZ[i], fma(-kz0, FZ[M * M + i], acc));
+        r[i] = fma(-mz1, FZ[FS + i], fma(-kz1, FZ[FS + M * M + i], acc));
+      }
+      fd_forward<K>(r, y);
+      T* R = WB + q * Z::WB + M * ln;
+#pragma unroll
+      for (int i = 0; i < M; ++i) R[i] = y[i];
+    }
+    __syncthreads();
+    // ---- local solve by fast diagonalisation (App. A.3), in place in WB ----
+    for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // forward y
+      const int q = idx / LINES, l = idx % LINES;
+      fd_smem_line<K, true>(WB + q * Z::WB + (l % M) + (l / M) * M * M, M);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // forward z, diagonal
+      const int q = idx / LINES, l = idx % LINES;
+      fd_smem_line<K, true, true>(WB + q * Z::WB + l, M * M, fa.dinv + l, M * M);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // backward z
+      const int q = idx / LINES, l = idx % LINES;
+      fd_smem_line<K, false>(WB + q * Z::WB + l, M * M);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // backward y
+      const int q = idx / LINES, l = idx % LINES;
+      fd_smem_line<K, false>(WB + q * Z::WB + (l % M) + (l / M) * M * M, M);
+    }
+    __syncthreads();
+    // ---- backward FD along x and scatter (eq. "scatter") ----
+    for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {
+      const int q = idx / LINES, l = idx % LINES;
+      const T* R = WB + q * Z::WB + M * l;
+      T yv[M], d[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) yv[i] = R[i];
+      fd_backward<K>(yv, d);
+      T* __restrict__ row = fa.u + s_origin[cur][q] + 1 + fa.py * (l % M + 1) + fa.pz * (l / M + 1);
+      if (om == T(1)) {
+#pragma unroll
+        for (int i = 0; i < M; ++i) row[i] = d[i];
+      } else {
+#pragma unroll
+        for (int i = 0; i < M; ++i) row[i] = fma(om, d[i], (T(1) - om) * row[i]);
+      }
+    }
+    async::fence_proxy_async();  // reads of the buffers before the next copies write them
+    __syncthreads();
+  }
+  if (!wait_ok) atomicExch(fa.err, GMG_ERR_TIMEOUT);
+}
+
+// ---- host side ----
+
+// patches per CTA, threads and input buffers of the shared-face sweep
+template <int K>
+struct FaceSweepCfg {
+  static constexpr int PPC = K == 3 ? 10 : K == 4 ? 5 : K == 5 ? 3 : K == 6 ? 2 : 1;
+  static constexpr int NT = K == 7 ? 192 : 256;
+  static constexpr int NBUF = K <= 4 || K == 7 ? 2 : 1;
+  static constexpr int SMEM = PPC * FaceSweepSmem<K>::per_patch(NBUF) * (int)sizeof(T) + 128;
+  static_assert(SMEM <= 227 * 1024, "shared-face sweep exceeds the shared memory of a CTA");
+  static_assert(PPC * (2 * K - 1) * (2 * K - 1) <= NT + 32 * 2, "lines per stage well above the threads");
+};
+constexpr int kFaceThreads = 128;
+
+static FaceGeom face_geom(const PatchLaunch& pl) {
+  FaceGeom fg;
+  fg.py = pl.g.py;
+  fg.pz = pl.g.pz;
+  for (int a = 0; a < 3; ++a) {
+    fg.first[a] = pl.first[a];
+    fg.count[a] = pl.count[a];
+  }
+  const long long cx = pl.count[0], cy = pl.count[1], cz = pl.count[2];
+  fg.nf[0] = (cx + 1) * cy * cz;
+  fg.nf[1] = cx * (cy + 1) * cz;
+  fg.nf[2] = cx * cy * (cz + 1);
+  const long long fs = face_fields(pl.g.k);
+  fg.foff[0] = 0;
+  fg.foff[1] = fg.nf[0] * fs;
+  fg.foff[2] = fg.foff[1] + fg.nf[1] * fs;
+  return fg;
+}
+
+template <int K>
+static int face_sweep_impl(const PatchLaunch& pl, T* u, const T* b, const T* dinv, T* faces, cudaStream_t s) {
+  using FC = FaceCfg<K, kFaceThreads>;
+  using SC = FaceSweepCfg<K>;
+  using Z = FaceSweepSmem<K>;
+  auto fk = face_kernel<K, kFaceThreads>;
+  auto pk = patch_face_kernel<K, SC::NT, SC::PPC, SC::NBUF>;
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    if (prepare(fk, FC::SMEM) != GMG_OK || prepare(pk, SC::SMEM) != GMG_OK) return GMG_ERR_CUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pk, SC::NT, SC::SMEM) != cudaSuccess ||
+        per_sm <= 0)
+      return GMG_ERR_CUDA;
+  }
+  const FaceGeom fg = face_geom(pl);
+  const long long bx = (fg.nf[0] + FC::FX - 1) / FC::FX, by = (fg.nf[1] + FC::FYZ - 1) / FC::FYZ,
+                  bz = (fg.nf[2] + FC::FYZ - 1) / FC::FYZ;
+  if (bx + by + bz > (1LL << 31) - 1) return GMG_ERR_UNSUPPORTED;
+  fk<<<(unsigned)(bx + by + bz), kFaceThreads, FC::SMEM, s>>>(u, faces, fg, (int)bx, (int)by);
+  count_launch();
+  if (cudaGetLastError() != cudaSuccess) return GMG_ERR_CUDA;
+
+  FaceSweepArgs fa;
+  fa.u = u;
+  fa.faces = faces;
+  fa.dinv = dinv;
+  fa.err = device_wait_flag();
+  if (!fa.err) return GMG_ERR_CUDA;
+  fa.py = pl.g.py;
+  fa.pz = pl.g.pz;
+  for (int a = 0; a < 3; ++a) {
+    fa.first[a] = pl.first[a];
+    fa.count[a] = pl.count[a];
+    fa.foff[a] = fg.foff[a];
+  }
+  fa.n_patches = pl.n_patches;
+  fa.ngroups = (pl.n_patches + SC::PPC - 1) / SC::PPC;
+  fa.sb = pl.sb;
+  fa.omega = pl.omega;
+  CUtensorMap bmap;
+  if (!tma_encode(&bmap, b, (int)sizeof(T), 3, pl.g.N, pl.g.py, pl.g.pz, Z::XB, Z::M)) return GMG_ERR_CUDA;
+  const int grid = std::min(fa.ngroups, per_sm * sm_count());
+  pk<<<grid, SC::NT, SC::SMEM, s>>>(fa, bmap);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+}
+
+// elements of the face buffer for one colour launch of pl's geometry
+inline long long face_buffer_elems(const PatchLaunch& pl) {
+  const FaceGeom fg = face_geom(pl);
+  return (fg.nf[0] + fg.nf[1] + fg.nf[2]) * face_fields(pl.g.k);
+}
+
+}  // namespace GMG_NS
+}  // namespace gmg

@@ -38,6 +38,7 @@ struct CreateOptions {
   void* finest_b = nullptr;
   void* finest_r = nullptr;
   bool no_cg = false;
+  bool no_faces = false;  // no face buffer (problems swept through tables only)
 };
 
 }  // namespace detail
@@ -93,6 +94,12 @@ struct gmg_problem {
   // skewed-slab schedule request: 0 whole colours, > 0 slab width in
   // vertex rows, -1 chosen per level to fit L2 (gmg_set_slab_width)
   int slab_width = 0;
+  // shared-face form of the FP64 3D sweep (degrees >= 3, whole colours):
+  // face buffer sized for the largest colour of the finest level and reused
+  // by every level (null: the closure form is used), and its switch
+  // (gmg_set_shared_faces)
+  void* faces = nullptr;
+  bool shared_faces = true;
   // CUDA graph of one outer-CG iteration (V-cycle preconditioner, dot
   // products, direction, FP64 operator, update) for the solution vector
   // cg_graph_u, captured on a private stream; dropped whenever anything the

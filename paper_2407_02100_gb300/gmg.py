@@ -34,7 +34,7 @@ EXPORTS = ["gmg_create", "gmg_destroy", "gmg_vector_layout", "gmg_level_info",
            "gmg_batch_cg_solve", "gmg_batch_autotune", "gmg_batch_set_ppc",
            "gmg_set_coefficient", "gmg_set_local_solver", "gmg_learned_train",
            "gmg_learned_corrections", "gmg_mlp_loss_grad", "gmg_tc_status", "gmg_tc_probe",
-           "gmg_set_slab_width", "gmg_slab_width"]
+           "gmg_set_slab_width", "gmg_slab_width", "gmg_set_shared_faces", "gmg_shared_faces"]
 GMG_LOCAL_FD_MEAN, GMG_LOCAL_LEARNED = 0, 1
 GMG_SWEEP_COMBINED, GMG_SWEEP_SEPARATED, GMG_SWEEP_BATCHED = 0, 1, 2
 
@@ -108,6 +108,8 @@ def lib():
             "gmg_tc_probe": [vp, vp, vp, i],
             "gmg_set_slab_width": [vp, i],
             "gmg_slab_width": [vp, i],
+            "gmg_set_shared_faces": [vp, i],
+            "gmg_shared_faces": [vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -289,6 +291,18 @@ def gmg_slab_width(h, level):
     if w < 0:
         raise GmgError("gmg_slab_width", w)
     return w
+
+
+def gmg_set_shared_faces(h, enable):
+    _check("gmg_set_shared_faces", lib().gmg_set_shared_faces(h, 1 if enable else 0))
+
+
+def gmg_shared_faces(h):
+    """1 if whole-colour FP64 3D sweeps of the problem use the shared-face form."""
+    r = lib().gmg_shared_faces(h)
+    if r < 0:
+        raise GmgError("gmg_shared_faces", r)
+    return r
 
 
 def gmg_tc_status():

@@ -29,9 +29,12 @@ def main():
     nodes = (a.n * a.degree + 1) ** a.dim
     out = {"dim": a.dim, "degree": a.degree, "n_cells": a.n, "nodes": nodes, "rtol": a.rtol}
     sols = {}
-    for name, prec in (("fp64", gmg.GMG_FP64), ("fp32_mixed", gmg.GMG_FP32), ("fp32_tc_mixed", gmg.GMG_FP32_TC),
-                       ("fp32_tf32_mixed", gmg.GMG_FP32_TF32)):
+    for name, prec in (("fp64", gmg.GMG_FP64), ("fp64_closure", gmg.GMG_FP64), ("fp32_mixed", gmg.GMG_FP32),
+                       ("fp32_tc_mixed", gmg.GMG_FP32_TC), ("fp32_tf32_mixed", gmg.GMG_FP32_TF32)):
         P = gmg.Problem(a.dim, a.degree, a.n, precision=prec)
+        # fp64: shared-face sweep where it applies (3D, k >= 3); fp64_closure:
+        # every patch residual on its own closure
+        gmg.gmg_set_shared_faces(P.h, name != "fp64_closure")
         b = P.to_device(rhs, dtype=torch.float64)
         u = P.zeros(dtype=torch.float64)
         gmg.cg_gmg_solve(P.h, u, b, a.rtol, 200)
@@ -51,7 +54,7 @@ def main():
         out[name] = {"time_to_solution_ms": ms, "mdofs": nodes / ms * 1e3 / 1e6,
                      "iterations": st.iterations, "final_rel_residual": res, "levels": P.n_levels}
         del P
-    for name in ("fp32_mixed", "fp32_tc_mixed", "fp32_tf32_mixed"):
+    for name in ("fp64_closure", "fp32_mixed", "fp32_tc_mixed", "fp32_tf32_mixed"):
         out[name]["rel_diff_vs_fp64_solution"] = float(
             torch.linalg.vector_norm(sols[name] - sols["fp64"]) / torch.linalg.vector_norm(sols["fp64"]))
         out["speedup_" + name] = out["fp64"]["time_to_solution_ms"] / out[name]["time_to_solution_ms"]

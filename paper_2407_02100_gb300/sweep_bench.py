@@ -32,12 +32,15 @@ def main():
                     help="time the sweep only (for captures of the sweep's kernels alone)")
     ap.add_argument("--slab", type=int, default=0,
                     help="skewed-slab width in vertex rows (0: one launch per colour, -1: fit L2)")
+    ap.add_argument("--closure", action="store_true",
+                    help="FP64 3D: evaluate every patch residual on its own closure (no shared faces)")
     a = ap.parse_args()
     build.build()
     prec = {"fp64": gmg.GMG_FP64, "fp32": gmg.GMG_FP32, "fp32_tc": gmg.GMG_FP32_TC,
             "fp32_tf32": gmg.GMG_FP32_TF32}[a.precision]
     P = gmg.Problem(a.dim, a.degree, a.n, n_levels=1, precision=prec)
     gmg.gmg_set_slab_width(P.h, a.slab)
+    gmg.gmg_set_shared_faces(P.h, not a.closure)
     u = P.to_device(inputs.random_nodal(a.dim, a.degree, a.n, 1))
     b = P.to_device(inputs.random_nodal(a.dim, a.degree, a.n, 2))
     y = P.zeros()
@@ -61,7 +64,7 @@ def main():
     nodes = (a.n * a.degree + 1) ** a.dim
     print(json.dumps({"dim": a.dim, "degree": a.degree, "n_cells": a.n, "precision": a.precision,
                       "variant": a.variant, "batch": a.batch if a.variant == "batched" else None,
-                      "slab_width": gmg.gmg_slab_width(P.h, 0),
+                      "slab_width": gmg.gmg_slab_width(P.h, 0), "shared_faces": gmg.gmg_shared_faces(P.h),
                       "nodes": nodes, "sweep_ms": t_sweep * 1e3, "sweep_mdofs": nodes / t_sweep / 1e6,
                       "apply_ms": t_apply * 1e3, "apply_mdofs": nodes / t_apply / 1e6}))
     P.close()
