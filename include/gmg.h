@@ -154,8 +154,8 @@ int gmg_smooth_colour(gmg_problem* p, int level, void* u, const void* b, int col
  * Algorithm 4 up to rounding); GMG_SWEEP_BATCHED = Algorithm 5, patches in
  * Z-curve order (Morton order of the vertex index, v_0 lowest bit) grouped by
  * colour and cut into batches of batch_size; for each batch index every
- * colour's batch in turn (equals Algorithm 4 when batch_size >= the largest
- * colour).  reverse != 0 reverses colours (and batches).  The first batched
+ * colour's batch in turn (bit for bit the closure form of Algorithm 4 when
+ * batch_size >= the largest colour; see gmg_set_shared_faces).  reverse != 0 reverses colours (and batches).  The first batched
  * call on a level allocates its patch list.  Errors: INVALID_ARG (unknown
  * variant, batch_size < 1), OOM, CUDA. */
 int gmg_smooth_variant(gmg_problem* p, int level, void* u, const void* b, int variant,
@@ -346,7 +346,9 @@ int gmg_patch_fd_1d(int degree, double* M, double* K, double* T, double* lambda)
  * slab, so consecutive launches touch about (W + 2) k node planes.  A patch
  * that overlaps one of an earlier colour position never lands in an earlier
  * slab, so every patch reads the values Algorithm 4 gives it: results are
- * bit-identical for every W.  width = 0 restores one launch per colour
+ * bit-identical for every W, and to whole colours in the closure form (for
+ * FP64 3D problems of degree >= 3 the whole-colour default is the
+ * shared-face form below, equal up to rounding).  width = 0 restores one launch per colour
  * (default); width = -1 picks per level the largest W whose node planes of u
  * and b fit in half of the L2 cache (W >= n - 1 + 2^d is one launch per
  * colour).  Constant-coefficient problems only (variable-coefficient ones

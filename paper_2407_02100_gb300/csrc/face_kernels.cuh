@@ -227,6 +227,7 @@ __global__ void __launch_bounds__(NT) face_kernel(const T* __restrict__ u, T* __
 //       closure kernel), then the face blocks X0 X1 Y0 Y1 Z0 Z1 of the patch
 //       (two M x M fields each, copied by cp.async.bulk); 128-byte multiple
 //   WB: the FD work (M^3)
+//   SUMS: Y0 + Y1 and Z0 + Z1 (4 M^2), the terms of the centre rows
 template <int K>
 struct FaceSweepSmem {
   static constexpr int C = 2 * K + 1, M = 2 * K - 1;
@@ -237,7 +238,8 @@ struct FaceSweepSmem {
   static constexpr int FS = face_fields(K);
   static constexpr int IN = (NBIN + 6 * FS + R128 - 1) / R128 * R128;
   static constexpr int WB = M * M * M;
-  static constexpr int per_patch(int nbuf) { return nbuf * IN + WB; }
+  static constexpr int SUMS = 2 * FS;
+  static constexpr int per_patch(int nbuf) { return nbuf * IN + WB + SUMS; }
   static constexpr int BOX_B = M * M * XB * (int)sizeof(T);
   static constexpr int FACE_BYTES = FS * (int)sizeof(T);
 };
@@ -272,6 +274,7 @@ __global__ void __launch_bounds__(NT) patch_face_kernel(const __grid_constant__ 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* const IN0 = reinterpret_cast<T*>(smem_raw + ((128 - (async::smem_u32(smem_raw) & 127)) & 127));
   T* const WB = IN0 + NBUF * PPC * Z::IN;
+  T* const SUMS = WB + PPC * Z::WB;
   __shared__ long long s_origin[2][PPC];
   __shared__ int s_x[2][PPC][3];     // closure origin (lattice coordinates)
   __shared__ long long s_face[2][PPC][6];  // element offsets of the six face blocks
@@ -357,21 +360,34 @@ __global__ void __launch_bounds__(NT) patch_face_kernel(const __grid_constant__ 
     const int nvalid = s_nvalid[cur];
     const T* IN = IN0 + cur * PPC * Z::IN;
 
+    // ---- centre rows: column 0 of the two-cell matrices is nonzero on rows
+    // 0..K-1 and column 2K on rows K-1..M-1, and on row K-1 (the vertex row)
+    // both equal the same cell-matrix entry, so a y (z) face term there is
+    // that entry times the sum of the two faces' fields ----
+    for (int idx = threadIdx.x; idx < nvalid * Z::SUMS; idx += NT) {
+      const int q = idx / Z::SUMS, e = idx % Z::SUMS;
+      const T* F = IN + q * Z::IN + Z::NBIN + (e < FS ? 2 * FS : 4 * FS) + e % FS;
+      SUMS[idx] = F[0] + F[FS];
+    }
+    __syncthreads();
+
     // ---- r = sb b - face contributions on interior x line (j, l), then the
     // forward FD transform along x; result into WB ----
     for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {
       const int q = idx / LINES, ln = idx % LINES, j = ln % M, l = ln / M;
       const T* P = IN + q * Z::IN;
       const T* Bq = P + s_x[cur][q][0] % Z::A + 1 + (l * M + j) * XB;
-      const T* FX = P + Z::NBIN;          // X0, X1: F1[l][j], F2[l][j]
-      const T* FY = FX + 2 * FS + l * M;   // Y0, Y1: G1[l][.], G2[l][.]
-      const T* FZ = FX + 4 * FS + j * M;   // Z0, Z1: H1[j][.], H2[j][.]
+      const T* FX = P + Z::NBIN;  // X0, X1: F1[l][j], F2[l][j]
+      // the y-face fields row j needs (G1[l][.], G2[l][.]: Y0, Y1 or their
+      // sum) and those of row l for the z faces (H1[j][.], H2[j][.])
+      const T* FY = (j < K - 1 ? FX + 2 * FS : j > K - 1 ? FX + 3 * FS : SUMS + q * Z::SUMS) + l * M;
+      const T* FZ = (l < K - 1 ? FX + 4 * FS : l > K - 1 ? FX + 5 * FS : SUMS + q * Z::SUMS + FS) + j * M;
       const T f10 = FX[l * M + j], f20 = FX[M * M + l * M + j];
       const T f11 = FX[FS + l * M + j], f21 = FX[FS + M * M + l * M + j];
-      // closure columns 0 and 2K of rows j (y faces) and l (z faces)
-      const int oj = off_patch(K) + j * C, ol = off_patch(K) + l * C;
-      const T my0 = c_Mp[oj], ky0 = c_Kp[oj], my1 = c_Mp[oj + C - 1], ky1 = c_Kp[oj + C - 1];
-      const T mz0 = c_Mp[ol], kz0 = c_Kp[ol], mz1 = c_Mp[ol + C - 1], kz1 = c_Kp[ol + C - 1];
+      // column 0 (rows up to K-1) or 2K of rows j and l
+      const int oj = off_patch(K) + j * C + (j < K ? 0 : C - 1);
+      const int ol = off_patch(K) + l * C + (l < K ? 0 : C - 1);
+      const T my = c_Mp[oj], ky = c_Kp[oj], mz = c_Mp[ol], kz = c_Kp[ol];
       T r[M], y[M];
 #pragma unroll
       for (int i = 0; i < M; ++i) {
@@ -380,10 +396,8 @@ __global__ void __launch_bounds__(NT) patch_face_kernel(const __grid_constant__ 
           acc = fma(-c_Kp[off_patch(K) + i * C], f10, fma(-c_Mp[off_patch(K) + i * C], f20, acc));
         if (band_hi(i + 1, K) == 2 * K)
           acc = fma(-c_Kp[off_patch(K) + i * C + C - 1], f11, fma(-c_Mp[off_patch(K) + i * C + C - 1], f21, acc));
-        acc = fma(-my0, FY[i], fma(-ky0, FY[M * M + i], acc));
-        acc = fma(-my1, FY[FS + i], fma(-ky1, FY[FS + M * M + i], acc));
-        acc = fma(-mz0, FZ[i], fma(-kz0, FZ[M * M + i], acc));
-        r[i] = fma(-mz1, FZ[FS + i], fma(-kz1, FZ[FS + M * M + i], acc));
+        acc = fma(-my, FY[i], fma(-ky, FY[M * M + i], acc));
+        r[i] = fma(-mz, FZ[i], fma(-kz, FZ[M * M + i], acc));
       }
       fd_forward<K>(r, y);
       T* R = WB + q * Z::WB + M * ln;
