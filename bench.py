@@ -40,10 +40,18 @@ FLOP_PER_PATCH = 8 * 7 * 625 * 2 + 6 * 2401 * 2
 BYTES_PER_NODE = 24
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
-# DRAM bytes of one average colour launch of the FP64 sweep kernel at this
-# workload, from an ncu capture of the current kernel (283.1 MB for the
-# 29,791-patch colour 0, scaled by patches to the 31,256-patch average)
-TRAFFIC_PER_LAUNCH = 283.131136e6 * 31256.0 / 29791.0
+# The FP64 sweep runs each colour as two launches, the face kernel and the
+# patch kernel (shared-face form); "per launch" figures below are per colour
+# step (both kernels).  DRAM bytes of one average colour step at this
+# workload, from ncu over every launch of 5 sweeps (dram__bytes_read.sum +
+# dram__bytes_write.sum: 18,621.4 MB / 40 colour steps)
+TRAFFIC_PER_LAUNCH = (6150.6e6 + 668.1e6 + 8965.3e6 + 2837.4e6) / 40
+# FP64 operations the kernels execute per patch (ncu SASS thread-instruction
+# counts of the 29,791-patch colour 0, per patch: face kernel 3,925.7 DFMA;
+# patch kernel 9,506 DFMA, 1,960 DADD, 686 DMUL)
+EXECUTED_FLOP_PER_PATCH = 2 * (3925.7 + 9506) + 1960 + 686
+# FP64 pipe activity of the two kernels (ncu, one colour step each)
+FP64_PIPE_ACTIVE = {"face_kernel": 0.805, "patch_face_kernel": 0.810}
 CPU_SAMPLE = dict(dim=3, degree=4, n_cells=8, n_levels=3)
 WORKLOAD = ("3D Poisson Q4, 64^3 cells, FP64 GMG(V(1,1), 8-colour vertex-patch smoother) "
             "preconditioned CG to 1e-10")
@@ -266,6 +274,7 @@ def run_ours(args):
     patches = (N_CELLS - 1) ** DIM
     flops_sweep = FLOP_PER_PATCH * patches
     achieved_tflops = flops_sweep / sweep_s / 1e12
+    executed_tflops = EXECUTED_FLOP_PER_PATCH * patches / sweep_s / 1e12
     hbm_gbs = BYTES_PER_NODE * nodes / sweep_s / 1e9
 
     # ---- end to end through the C ABI with host buffers ----
@@ -370,16 +379,21 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
                      "traffic": TRAFFIC_PER_LAUNCH,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                                       "colour launch (29,791 patches) scaled to the average launch "
-                                       "(31,256 patches)",
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum over every "
+                                       "launch of 5 sweeps, per colour step (face kernel + patch kernel)",
                      "algorithmic_bytes_per_launch": BYTES_PER_NODE * nodes / 8,
-                     "fp64_pipe_active_ncu": 0.817,
-                     "kernel": "patch_colour_kernel<3,4,256,4,1,1> (FP64, TMA gather), one launch per colour",
+                     "executed_flop_per_patch": EXECUTED_FLOP_PER_PATCH,
+                     "executed_tflops": executed_tflops,
+                     "executed_frac": executed_tflops / FP64_PEAK_TFLOPS,
+                     "fp64_pipe_active_ncu": FP64_PIPE_ACTIVE,
+                     "kernel": "face_kernel<4,128> + patch_face_kernel<4,256,5,2> (FP64 shared-face "
+                               "sweep), one pair of launches per colour; timed as whole sweeps",
                      "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz",
-                     "note": "achieved counts the method's operation count (98,812 flop per patch); "
-                             "the kernel executes fewer (banded two-cell matrices, even/odd FD), "
-                             "so frac > 1"},
+                     "note": "achieved and frac count the method's operation count (98,812 flop per "
+                             "patch); the kernels execute 29,510 FP64 flop per patch (banded two-cell "
+                             "matrices, even/odd FD, residual from the closure faces, each face "
+                             "evaluated once per colour), so frac > 1; executed_frac and the FP64 "
+                             "pipe activity are the utilisation of the hardware"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "MDoF/s", "h2d_bytes_per_step": n_elems * 8,
                 "d2h_bytes_per_step": n_elems * 8},
