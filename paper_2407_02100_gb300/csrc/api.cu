@@ -94,8 +94,10 @@ int apply_level(gmg_problem* p, int level, const void* x, void* y, const void* b
   al.g = L.g;
   al.alpha = alpha;
   al.beta = beta;
-  if (p->esize == 8)
+  if (p->esize == 8) {
+    al.ws = p->apply_ws;
     return launch_apply<double>(al, (const double*)x, (double*)y, (const double*)bvec, p->stream);
+  }
   return launch_apply<float>(al, (const float*)x, (float*)y, (const float*)bvec, p->stream);
 }
 
@@ -609,6 +611,12 @@ int gmg::detail::create_problem(const gmg_desc* d, gmg_problem* p, const CreateO
       fe = std::max(fe, face_buffer_elems(colour_launch(p->levels[L - 1], c, d->damping)));
     if (fe > 0 && dalloc(p, &p->faces, fe * 8) != GMG_OK) p->faces = nullptr;
   }
+  // workspace of the three-pass FP64 operator (also used by the FP64 CG of
+  // single-precision problems): four finest-level vectors; without memory
+  // for it the tile kernel is used
+  if (staged_apply_preferred(dim, k) && !opt.no_faces &&
+      dalloc(p, &p->apply_ws, 4 * p->levels[L - 1].n_elems * 8) != GMG_OK)
+    p->apply_ws = nullptr;
   // transfer tables
   std::vector<double> P1;
   prolongation_cell_1d(k, P1);  // (2k+1) x (k+1)
@@ -755,6 +763,7 @@ int gmg_apply_operator_f64(gmg_problem* p, int level, const double* x, double* y
   al.g = L.g;
   al.alpha = op_scale(L);
   al.beta = 0.0;
+  al.ws = p->apply_ws;
   return launch_apply<double>(al, x, y, nullptr, p->stream);
 }
 
@@ -937,6 +946,7 @@ int cg_gmg_solve(gmg_problem* p, double* u, const double* b, double rtol, int ma
     al.g = F.g;
     al.alpha = sign * op_scale(F);
     al.beta = beta;
+    al.ws = p->apply_ws;
     return launch_apply<double>(al, x, y, z, s);
   };
   // r = b - A u

@@ -63,7 +63,13 @@ struct PatchTable {
 struct ApplyLaunch {
   LevelGeom g;
   double alpha, beta;
+  // FP64 3D: four level vectors of workspace (pz * N doubles each) for the
+  // halo-free three-pass form, or null for the tile kernel
+  void* ws = nullptr;
 };
+// whether launch_apply<double> uses the three-pass form in 3D at degree k
+// when given a workspace
+bool staged_apply_preferred(int dim, int k);
 
 // One 1D contraction along `axis` of a (up to) 3-index array:
 //   out[o + out_off] (+)= sum_w coef[(o_ax % R) * W + w] * in[i]

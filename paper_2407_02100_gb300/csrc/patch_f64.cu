@@ -25,4 +25,6 @@ int launch_patch_faces(const PatchLaunch& pl, double* u, const double* b, const 
 
 long long face_buffer_elems(const PatchLaunch& pl) { return f64::face_buffer_elems(pl); }
 
+bool staged_apply_preferred(int dim, int k) { return dim == 3 && f64::staged_apply_degree(k); }
+
 }  // namespace gmg

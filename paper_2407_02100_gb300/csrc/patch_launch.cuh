@@ -6,6 +6,7 @@
 
 #include "../../include/gmg.h"
 #include "tma_host.h"
+#include "staged_apply.cuh"
 
 namespace gmg {
 namespace GMG_NS {
@@ -210,8 +211,13 @@ static int apply_cfg(const ApplyLaunch& al, const T* x, T* y, const T* bvec, cud
   return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
 }
 
+// degrees at which the FP64 3D three-pass form beats the tile kernel
+constexpr bool staged_apply_degree(int k) { return k >= 3; }
+
 template <int DIM, int K>
 static int apply_impl(const ApplyLaunch& al, const T* x, T* y, const T* bvec, cudaStream_t s) {
+  if constexpr (DIM == 3 && sizeof(T) == 8 && staged_apply_degree(K))
+    if (al.ws) return staged_apply_impl<K>(al, x, y, bvec, s);
   using Cfg = ApplyCfg<DIM, K>;
   static_assert(ApplyDims<DIM, K, Cfg::BX, Cfg::BY, Cfg::BZ>::SMEM_BYTES <= 227 * 1024,
                 "operator tile exceeds the shared memory of a CTA");

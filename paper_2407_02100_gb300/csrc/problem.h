@@ -38,7 +38,7 @@ struct CreateOptions {
   void* finest_b = nullptr;
   void* finest_r = nullptr;
   bool no_cg = false;
-  bool no_faces = false;  // no face buffer (problems swept through tables only)
+  bool no_faces = false;  // no face buffer or operator workspace (batch members)
 };
 
 }  // namespace detail
@@ -100,6 +100,9 @@ struct gmg_problem {
   // (gmg_set_shared_faces)
   void* faces = nullptr;
   bool shared_faces = true;
+  // workspace of the three-pass FP64 3D operator (four finest-level
+  // vectors), null where the tile kernel is used
+  void* apply_ws = nullptr;
   // CUDA graph of one outer-CG iteration (V-cycle preconditioner, dot
   // products, direction, FP64 operator, update) for the solution vector
   // cg_graph_u, captured on a private stream; dropped whenever anything the
