@@ -385,6 +385,23 @@ int gmg_slab_width(const gmg_problem* p, int level);
 int gmg_set_shared_faces(gmg_problem* p, int enable);
 int gmg_shared_faces(const gmg_problem* p);
 
+/* ---- Three-pass FP64 operator -------------------------------------------
+ * In 3D at degree >= 3 the FP64 level operator (gmg_apply_operator(_f64),
+ * the V-cycle residuals of FP64 problems and the FP64 CG of every problem)
+ * runs as three passes over the level, one 1D contraction per axis with the
+ * global 1D mass and stiffness matrices (z, then y, then x), through four
+ * workspace vectors of the finest level (FP64, allocated by gmg_create).
+ * Every output row is evaluated once; the tile kernel recomputes a halo of
+ * up to k + 1 nodes per direction.  Same operator, results equal up to
+ * rounding.  If the workspace cannot be allocated the tile kernel is used.
+ * gmg_set_three_pass_operator: enable (default) or disable the form (the
+ *   workspace stays allocated); GMG_ERR_INVALID_ARG for a null problem.
+ * gmg_three_pass_operator: 1 if the FP64 operator of the problem uses the
+ *   form (enabled and the workspace allocated), 0 if not,
+ *   GMG_ERR_INVALID_ARG for a null problem. */
+int gmg_set_three_pass_operator(gmg_problem* p, int enable);
+int gmg_three_pass_operator(const gmg_problem* p);
+
 /* ---- Tensor-core sweep (GMG_FP32_TC) and bounded device waits ----------
  * Every patch of one colour is processed as in gmg_smooth (Algorithm 4,
  * local_update of Sec. 3.1: gather, local residual by sum factorisation,

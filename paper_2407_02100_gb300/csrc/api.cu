@@ -95,7 +95,7 @@ int apply_level(gmg_problem* p, int level, const void* x, void* y, const void* b
   al.alpha = alpha;
   al.beta = beta;
   if (p->esize == 8) {
-    al.ws = p->apply_ws;
+    al.ws = p->op_ws();
     return launch_apply<double>(al, (const double*)x, (double*)y, (const double*)bvec, p->stream);
   }
   return launch_apply<float>(al, (const float*)x, (float*)y, (const float*)bvec, p->stream);
@@ -763,7 +763,7 @@ int gmg_apply_operator_f64(gmg_problem* p, int level, const double* x, double* y
   al.g = L.g;
   al.alpha = op_scale(L);
   al.beta = 0.0;
-  al.ws = p->apply_ws;
+  al.ws = p->op_ws();
   return launch_apply<double>(al, x, y, nullptr, p->stream);
 }
 
@@ -848,6 +848,18 @@ int gmg_set_local_solver(gmg_problem* p, int solver) {
     return GMG_OK;
   }
   return GMG_ERR_INVALID_ARG;
+}
+
+int gmg_set_three_pass_operator(gmg_problem* p, int enable) {
+  if (!p) return GMG_ERR_INVALID_ARG;
+  drop_cg_graph(p);
+  p->three_pass = enable != 0;
+  return GMG_OK;
+}
+
+int gmg_three_pass_operator(const gmg_problem* p) {
+  if (!p) return GMG_ERR_INVALID_ARG;
+  return p->op_ws() ? 1 : 0;
 }
 
 int gmg_set_shared_faces(gmg_problem* p, int enable) {
@@ -946,7 +958,7 @@ int cg_gmg_solve(gmg_problem* p, double* u, const double* b, double rtol, int ma
     al.g = F.g;
     al.alpha = sign * op_scale(F);
     al.beta = beta;
-    al.ws = p->apply_ws;
+    al.ws = p->op_ws();
     return launch_apply<double>(al, x, y, z, s);
   };
   // r = b - A u

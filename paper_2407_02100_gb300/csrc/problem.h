@@ -103,6 +103,8 @@ struct gmg_problem {
   // workspace of the three-pass FP64 3D operator (four finest-level
   // vectors), null where the tile kernel is used
   void* apply_ws = nullptr;
+  bool three_pass = true;  // gmg_set_three_pass_operator
+  void* op_ws() const { return three_pass ? apply_ws : nullptr; }
   // CUDA graph of one outer-CG iteration (V-cycle preconditioner, dot
   // products, direction, FP64 operator, update) for the solution vector
   // cg_graph_u, captured on a private stream; dropped whenever anything the

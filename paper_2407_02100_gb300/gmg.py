@@ -34,7 +34,8 @@ EXPORTS = ["gmg_create", "gmg_destroy", "gmg_vector_layout", "gmg_level_info",
            "gmg_batch_cg_solve", "gmg_batch_autotune", "gmg_batch_set_ppc",
            "gmg_set_coefficient", "gmg_set_local_solver", "gmg_learned_train",
            "gmg_learned_corrections", "gmg_mlp_loss_grad", "gmg_tc_status", "gmg_tc_probe",
-           "gmg_set_slab_width", "gmg_slab_width", "gmg_set_shared_faces", "gmg_shared_faces"]
+           "gmg_set_slab_width", "gmg_slab_width", "gmg_set_shared_faces", "gmg_shared_faces",
+           "gmg_set_three_pass_operator", "gmg_three_pass_operator"]
 GMG_LOCAL_FD_MEAN, GMG_LOCAL_LEARNED = 0, 1
 GMG_SWEEP_COMBINED, GMG_SWEEP_SEPARATED, GMG_SWEEP_BATCHED = 0, 1, 2
 
@@ -110,6 +111,8 @@ def lib():
             "gmg_slab_width": [vp, i],
             "gmg_set_shared_faces": [vp, i],
             "gmg_shared_faces": [vp],
+            "gmg_set_three_pass_operator": [vp, i],
+            "gmg_three_pass_operator": [vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -302,6 +305,18 @@ def gmg_shared_faces(h):
     r = lib().gmg_shared_faces(h)
     if r < 0:
         raise GmgError("gmg_shared_faces", r)
+    return r
+
+
+def gmg_set_three_pass_operator(h, enable):
+    _check("gmg_set_three_pass_operator", lib().gmg_set_three_pass_operator(h, 1 if enable else 0))
+
+
+def gmg_three_pass_operator(h):
+    """1 if the FP64 operator of the problem runs as three passes (3D, k >= 3)."""
+    r = lib().gmg_three_pass_operator(h)
+    if r < 0:
+        raise GmgError("gmg_three_pass_operator", r)
     return r
 
 

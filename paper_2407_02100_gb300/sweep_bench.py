@@ -34,6 +34,8 @@ def main():
                     help="skewed-slab width in vertex rows (0: one launch per colour, -1: fit L2)")
     ap.add_argument("--closure", action="store_true",
                     help="FP64 3D: evaluate every patch residual on its own closure (no shared faces)")
+    ap.add_argument("--tile-operator", action="store_true",
+                    help="FP64 3D: time the tile kernel instead of the three-pass operator")
     a = ap.parse_args()
     build.build()
     prec = {"fp64": gmg.GMG_FP64, "fp32": gmg.GMG_FP32, "fp32_tc": gmg.GMG_FP32_TC,
@@ -41,6 +43,7 @@ def main():
     P = gmg.Problem(a.dim, a.degree, a.n, n_levels=1, precision=prec)
     gmg.gmg_set_slab_width(P.h, a.slab)
     gmg.gmg_set_shared_faces(P.h, not a.closure)
+    gmg.gmg_set_three_pass_operator(P.h, not a.tile_operator)
     u = P.to_device(inputs.random_nodal(a.dim, a.degree, a.n, 1))
     b = P.to_device(inputs.random_nodal(a.dim, a.degree, a.n, 2))
     y = P.zeros()
@@ -65,6 +68,7 @@ def main():
     print(json.dumps({"dim": a.dim, "degree": a.degree, "n_cells": a.n, "precision": a.precision,
                       "variant": a.variant, "batch": a.batch if a.variant == "batched" else None,
                       "slab_width": gmg.gmg_slab_width(P.h, 0), "shared_faces": gmg.gmg_shared_faces(P.h),
+                      "three_pass_operator": gmg.gmg_three_pass_operator(P.h),
                       "nodes": nodes, "sweep_ms": t_sweep * 1e3, "sweep_mdofs": nodes / t_sweep / 1e6,
                       "apply_ms": t_apply * 1e3, "apply_mdofs": nodes / t_apply / 1e6}))
     P.close()
