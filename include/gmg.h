@@ -360,8 +360,10 @@ int gmg_set_slab_width(gmg_problem* p, int width);
  * negative status. */
 int gmg_slab_width(const gmg_problem* p, int level);
 
-/* ---- Shared-face form of the FP64 3D sweep -------------------------------
- * Constant-coefficient FP64 problems in 3D of degree >= 3 evaluate the local
+/* ---- Shared-face form of the 3D sweep ------------------------------------
+ * Constant-coefficient 3D problems in FP64 of degree >= 3, and in GMG_FP32 of
+ * degree >= 7 (below that the FP32 closure kernel measured faster), evaluate
+ * the local
  * residual of a whole-colour sweep (Algorithm 4) from the closure boundary
  * only: the local solver is exact (App. A.3), so the new interior is
  * A_j^{-1}(b_j - bar A_j bar u_j^0) with the patch interior of bar u_j^0 set
@@ -373,13 +375,13 @@ int gmg_slab_width(const gmg_problem* p, int level);
  * patch kernel reads them.  Same method and colour order; results agree
  * with the closure form up to rounding.  The face buffer (allocated by
  * gmg_create: 12 (2k-1)^2 doubles per patch of the finest level's largest
- * colour, about 0.6x a level vector at k = 4) is shared by all levels; if it
- * cannot be allocated the closure form is used.  Algorithm 3 and 5, slab
- * schedules, batches and single-precision problems always use the closure
- * form.
+ * colour, about 0.6x a level vector at k = 4, in the problem precision) is
+ * shared by all levels; if it cannot be allocated the closure form is used.
+ * Algorithm 3 and 5, slab schedules, batches and the tensor-core precisions
+ * always use the closure form (or their own kernel).
  * gmg_set_shared_faces: enable (default) or disable the form; returns
  *   GMG_ERR_INVALID_ARG for a null problem.
- * gmg_shared_faces: 1 if whole-colour FP64 3D sweeps of the problem use the
+ * gmg_shared_faces: 1 if whole-colour 3D sweeps of the problem use the
  *   form (enabled and the buffer allocated), 0 if not, GMG_ERR_INVALID_ARG
  *   for a null problem. */
 int gmg_set_shared_faces(gmg_problem* p, int enable);

@@ -130,13 +130,18 @@ int launch_colour(gmg_problem* p, const PatchLaunch& pl, void* u, const void* b)
   if (pl.n_patches == 0) return GMG_OK;
   if (p->esize == 8) {
     if (p->faces && p->shared_faces) {
-      const int st = launch_patch_faces(pl, (double*)u, (const double*)b, (const double*)p->dinv,
-                                        (double*)p->faces, p->stream);
+      const int st = launch_patch_faces<double>(pl, (double*)u, (const double*)b, (const double*)p->dinv,
+                                                (double*)p->faces, p->stream);
       if (st != GMG_ERR_UNSUPPORTED) return st;
     }
     return launch_patch_colour<double>(pl, (double*)u, (const double*)b, (const double*)p->dinv, p->stream);
   }
   const int pr = p->desc.precision;
+  if (pr == GMG_FP32 && p->faces && p->shared_faces) {
+    const int st = launch_patch_faces<float>(pl, (float*)u, (const float*)b, (const float*)p->dinv,
+                                             (float*)p->faces, p->stream);
+    if (st != GMG_ERR_UNSUPPORTED) return st;
+  }
   if ((pr == GMG_FP32_TC || pr == GMG_FP32_TF32) && pl.mode == 0 && tc_supported(pl.g.dim, pl.g.k))
     return launch_patch_tc(pl, (float*)u, (const float*)b, (const float*)p->dinv, pr == GMG_FP32_TC, p->stream);
   return launch_patch_colour<float>(pl, (float*)u, (const float*)b, (const float*)p->dinv, p->stream);
@@ -603,13 +608,21 @@ int gmg::detail::create_problem(const gmg_desc* d, gmg_problem* p, const CreateO
     dinv[t] = 1.0 / s;
   }
   CHECK(upload_table(p, &p->dinv, dinv));
-  // face buffer of the shared-face FP64 sweep: the largest colour of the
-  // finest level; without memory for it the closure form is used
-  if (p->esize == 8 && dim == 3 && k >= 3 && !opt.no_faces) {
+  // face buffer of the shared-face sweep: the largest colour of the finest
+  // level; without memory for it the closure form is used.  FP64 problems
+  // use the form from k = 3 (the sweep is bound by FP64 instructions, which
+  // it cuts by a third); FP32 ones from k = 7: at k = 3, 4 the FP32 closure
+  // kernel is faster (it is bound by issue and latency, and the face pass
+  // adds a launch and its traffic per colour), at k = 7 the form is 11 %
+  // faster.  The tensor-core precisions keep their kernel.
+  const bool faces_form = d->precision == GMG_FP64 ? k >= 3 : d->precision == GMG_FP32 && k >= 7;
+  if (faces_form && dim == 3 && !opt.no_faces) {
     long long fe = 0;
-    for (int c = 0; c < (1 << dim); ++c)
-      fe = std::max(fe, face_buffer_elems(colour_launch(p->levels[L - 1], c, d->damping)));
-    if (fe > 0 && dalloc(p, &p->faces, fe * 8) != GMG_OK) p->faces = nullptr;
+    for (int c = 0; c < (1 << dim); ++c) {
+      const PatchLaunch pl = colour_launch(p->levels[L - 1], c, d->damping);
+      fe = std::max(fe, p->esize == 8 ? face_buffer_elems<double>(pl) : face_buffer_elems<float>(pl));
+    }
+    if (fe > 0 && dalloc(p, &p->faces, fe * p->esize) != GMG_OK) p->faces = nullptr;
   }
   // workspace of the three-pass FP64 operator (also used by the FP64 CG of
   // single-precision problems): four finest-level vectors; without memory

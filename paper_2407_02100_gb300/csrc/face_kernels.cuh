@@ -1,6 +1,7 @@
-// Shared-face form of the FP64 3D patch sweep (combined colourised smoother,
+// Shared-face form of the 3D patch sweep (combined colourised smoother,
 // Algorithm 4, constant coefficient, degrees 3..8).  Included by patch_f64.cu
-// after patch_kernels.cuh and patch_launch.cuh (T = double).
+// and patch_f32.cu after patch_kernels.cuh and patch_launch.cuh (T = double
+// or float).
 //
 // The local solver is exact, so the updated interior of patch j is
 // A_j^{-1} (b_j - bar A_j bar u_j^0), bar u_j^0 its closure with the interior
@@ -36,7 +37,8 @@ namespace GMG_NS {
 //   z faces fz = i_z, i_z + 1 of Z[(fz c_y + i_y) c_x + i_x].
 // Each face holds two M x M fields: x faces F1, F2 as [l][j] (l the z row,
 // j the y row), y faces G1, G2 as [l][i], z faces H1, H2 as [j][i]
-// (i the x row); the families start at foff[0..2] elements.
+// (i the x row), padded to a multiple of 16 bytes (face_fields elements);
+// the families start at foff[0..2] elements.
 struct FaceGeom {
   long long py, pz;
   int first[3], count[3];
@@ -44,7 +46,9 @@ struct FaceGeom {
   long long foff[3];
 };
 
-__host__ __device__ constexpr int face_fields(int k) { return 2 * (2 * k - 1) * (2 * k - 1); }
+__host__ __device__ constexpr int face_fields(int k) {
+  return (2 * (2 * k - 1) * (2 * k - 1) + 16 / (int)sizeof(T) - 1) / (16 / (int)sizeof(T)) * (16 / (int)sizeof(T));
+}
 
 // acc + sum over the interior columns of row i of M_p (KIND 0) or K_p
 // (KIND 1), x[a] the value at interior column a (closure column a + 1)
@@ -225,9 +229,11 @@ __global__ void __launch_bounds__(NT) face_kernel(const T* __restrict__ u, T* __
 // Shared-memory plan of the shared-face sweep, per patch (doubles):
 //   IN (NBUF copies): interior rows of b (TMA box rows of XB, as in the
 //       closure kernel), then the face blocks X0 X1 Y0 Y1 Z0 Z1 of the patch
-//       (two M x M fields each, copied by cp.async.bulk); 128-byte multiple
+//       (two M x M fields each, padded to 16 bytes, copied by
+//       cp.async.bulk); 128-byte multiple
 //   WB: the FD work (M^3)
-//   SUMS: Y0 + Y1 and Z0 + Z1 (4 M^2), the terms of the centre rows
+//   SUMS: Y0 + Y1 and Z0 + Z1 (two padded face blocks), the terms of the
+//   centre rows
 template <int K>
 struct FaceSweepSmem {
   static constexpr int C = 2 * K + 1, M = 2 * K - 1;
@@ -530,10 +536,36 @@ static int face_sweep_impl(const PatchLaunch& pl, T* u, const T* b, const T* din
 }
 
 // elements of the face buffer for one colour launch of pl's geometry
-inline long long face_buffer_elems(const PatchLaunch& pl) {
+inline long long face_buffer_elems_t(const PatchLaunch& pl) {
   const FaceGeom fg = face_geom(pl);
   return (fg.nf[0] + fg.nf[1] + fg.nf[2]) * face_fields(pl.g.k);
 }
 
 }  // namespace GMG_NS
+}  // namespace gmg
+
+namespace gmg {
+
+template <>
+int launch_patch_faces<GMG_T>(const PatchLaunch& pl, GMG_T* u, const GMG_T* b, const GMG_T* dinv, GMG_T* faces,
+                              cudaStream_t s) {
+  if (pl.g.dim != 3 || pl.g.k < 3 || pl.g.k > 8 || pl.mode != 0 || pl.plist || !faces)
+    return GMG_ERR_UNSUPPORTED;
+  if (!tma_vector_ok(b, (int)sizeof(GMG_T), 3, pl.g.py, pl.g.pz)) return GMG_ERR_UNSUPPORTED;
+  if (pl.n_patches <= 0) return GMG_OK;
+  switch (pl.g.k) {
+    case 3: return GMG_NS::face_sweep_impl<3>(pl, u, b, dinv, faces, s);
+    case 4: return GMG_NS::face_sweep_impl<4>(pl, u, b, dinv, faces, s);
+    case 5: return GMG_NS::face_sweep_impl<5>(pl, u, b, dinv, faces, s);
+    case 6: return GMG_NS::face_sweep_impl<6>(pl, u, b, dinv, faces, s);
+    case 7: return GMG_NS::face_sweep_impl<7>(pl, u, b, dinv, faces, s);
+    default: return GMG_NS::face_sweep_impl<8>(pl, u, b, dinv, faces, s);
+  }
+}
+
+template <>
+long long face_buffer_elems<GMG_T>(const PatchLaunch& pl) {
+  return GMG_NS::face_buffer_elems_t(pl);
+}
+
 }  // namespace gmg

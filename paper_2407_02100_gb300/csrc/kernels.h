@@ -121,12 +121,13 @@ int launch_patch_tc(const PatchLaunch& pl, float* u, const float* b, const float
 int launch_patch_table_tc(int dim, int k, const PatchLaunch* pls, float* const* us, const float* const* bs,
                           int n, const float* dinv, bool split, cudaStream_t s);
 
-// Shared-face form of the FP64 3D sweep of one whole colour (face kernel,
-// then patch kernel; faces: a buffer of face_buffer_elems(pl) doubles).
+// Shared-face form of the 3D sweep of one whole colour (face kernel, then
+// patch kernel; faces: a buffer of face_buffer_elems<T>(pl) elements).
 // GMG_ERR_UNSUPPORTED when the form does not apply (2D, k < 3, solve-only
 // mode, a patch list, or a b vector the TMA box cannot address).
-int launch_patch_faces(const PatchLaunch& pl, double* u, const double* b, const double* dinv, double* faces,
-                       cudaStream_t s);
+template <typename T>
+int launch_patch_faces(const PatchLaunch& pl, T* u, const T* b, const T* dinv, T* faces, cudaStream_t s);
+template <typename T>
 long long face_buffer_elems(const PatchLaunch& pl);
 
 template <typename T>

@@ -3,3 +3,4 @@
 #define GMG_NS f32
 #include "patch_kernels.cuh"
 #include "patch_launch.cuh"
+#include "face_kernels.cuh"

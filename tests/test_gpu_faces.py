@@ -1,10 +1,13 @@
-"""Shared-face form of the FP64 3D sweep (degrees >= 3) through the C ABI.
+"""Shared-face form of the 3D sweep (degrees >= 3; FP64 and FP32 problems)
+through the C ABI.
 
 The local solver is exact, so a patch's new interior depends on its closure
 boundary only; the form evaluates each face plane's two-dimensional
 sum-factorised terms once per colour and lets both patches that share the
 plane read them.  It is the same method as the closure form: both are
-compared with the oracle (FP64, relative 1e-12) and with each other."""
+compared with the oracle (FP64: relative 1e-12; FP32, used from k = 7: no
+more than twice the closure form's own FP32 error, both about
+eps_32 cond(A_j), cond(A_j) = 174 at k = 7) and with each other."""
 import numpy as np
 import pytest
 
@@ -34,7 +37,9 @@ def test_form_is_used_where_it_applies(gmg):
     assert gmg.gmg_shared_faces(gmg.Problem(3, 3, 4).h) == 1
     assert gmg.gmg_shared_faces(gmg.Problem(3, 2, 4, n_levels=1).h) == 0      # k < 3
     assert gmg.gmg_shared_faces(gmg.Problem(2, 4, 4, n_levels=1).h) == 0      # 2D
-    assert gmg.gmg_shared_faces(gmg.Problem(3, 4, 4, n_levels=1, precision=1).h) == 0
+    assert gmg.gmg_shared_faces(gmg.Problem(3, 4, 4, n_levels=1, precision=gmg.GMG_FP32).h) == 0
+    assert gmg.gmg_shared_faces(gmg.Problem(3, 7, 2, n_levels=1, precision=gmg.GMG_FP32).h) == 1
+    assert gmg.gmg_shared_faces(gmg.Problem(3, 4, 4, n_levels=1, precision=gmg.GMG_FP32_TC).h) == 0
     P = gmg.Problem(3, 4, 4, n_levels=1)
     gmg.gmg_set_shared_faces(P.h, False)
     assert gmg.gmg_shared_faces(P.h) == 0
@@ -131,3 +136,61 @@ def test_pcg_iterations_and_solution(gmg, k, n):
     gmg.gmg_set_shared_faces(P.h, True)
     assert its[0] == its[1]
     assert rel(sols[0], sols[1]) <= 1e-11
+
+
+@pytest.mark.parametrize("k,n", [(7, 3), (8, 2), (7, 2)])
+def test_fp32_each_colour_matches_oracle(gmg, k, n):
+    """FP32 data (the oracle takes the FP32-rounded inputs): each colour step
+    of the form is as close to the oracle as the closure kernel's."""
+    m = Mesh(3, k, n)
+    s = PatchSmoother(m)
+    P = gmg.Problem(3, k, n, n_levels=1, precision=gmg.GMG_FP32)
+    assert gmg.gmg_shared_faces(P.h) == 1
+    u0 = inputs.random_nodal(3, k, n, 7501).astype(np.float32).astype(np.float64)
+    b = inputs.random_nodal(3, k, n, 7502).astype(np.float32).astype(np.float64)
+    bd = P.to_device(b)
+    for c in range(m.n_colours):
+        ref = s.colour_step(u0.copy(), b, c)
+        err = []
+        for on in (True, False):
+            gmg.gmg_set_shared_faces(P.h, on)
+            ud = P.to_device(u0)
+            gmg.gmg_smooth_colour(P.h, 0, ud, bd, c)
+            err.append(rel(P.from_device(ud), ref))
+        gmg.gmg_set_shared_faces(P.h, True)
+        assert err[0] <= 2 * err[1] + 1e-6 and err[0] <= 1e-4, (c, err)
+
+
+@pytest.mark.parametrize("k,n,omega", [(7, 3, 1.0), (7, 2, 0.8), (8, 2, 1.0)])
+def test_fp32_face_and_closure_forms_agree(gmg, k, n, omega):
+    P = gmg.Problem(3, k, n, n_levels=1, precision=gmg.GMG_FP32, damping=omega)
+    u0 = inputs.random_nodal(3, k, n, 7601)
+    bd = P.to_device(inputs.random_nodal(3, k, n, 7602))
+    out = []
+    for on in (True, False):
+        gmg.gmg_set_shared_faces(P.h, on)
+        ud = P.to_device(u0)
+        gmg.gmg_smooth(P.h, 0, ud, bd, 2, False)
+        out.append(P.from_device(ud))
+    gmg.gmg_set_shared_faces(P.h, True)
+    assert rel(out[0], out[1]) <= 3e-5
+
+
+@pytest.mark.parametrize("k,n", [(7, 4)])
+def test_fp32_mixed_pcg_iterations(gmg, k, n):
+    """FP32 V-cycle inside FP64 CG: same iterations and solution (to the
+    solve's tolerance) with either form of the FP32 sweep."""
+    import torch
+    P = gmg.Problem(3, k, n, precision=gmg.GMG_FP32)
+    b = P.to_device(inputs.random_nodal(3, k, n, 7701), dtype=torch.float64)
+    sols, its = [], []
+    for on in (True, False):
+        gmg.gmg_set_shared_faces(P.h, on)
+        u = P.zeros(dtype=torch.float64)
+        _, st = gmg.cg_gmg_solve(P.h, u, b, 1e-10, 100)
+        assert st.converged == 1 and st.relative_residual <= 1e-10
+        sols.append(P.from_device(u))
+        its.append(st.iterations)
+    gmg.gmg_set_shared_faces(P.h, True)
+    assert abs(its[0] - its[1]) <= 1, its
+    assert rel(sols[0], sols[1]) <= 1e-8
