@@ -40,6 +40,10 @@ struct gmg_batch {
   double *rz = nullptr, *pq = nullptr, *rr = nullptr, *rzn = nullptr, *bb = nullptr;
   int* active = nullptr;
   double* partial = nullptr;
+  // workspace of the three-pass FP64 operator, sized for the largest
+  // problem and shared (the problems' operators run one after another on
+  // the batch stream); null: the tile kernel
+  void* apply_ws = nullptr;
   Segments seg;
   int ppc = 0;                  // tuned patches per CTA of the batched sweep (0 = default)
   cudaStream_t cap_stream = nullptr;  // private stream the graph is captured on
@@ -211,6 +215,7 @@ int batch_apply_f64(gmg_batch* B, const double* x, double* y, const double* z, d
     al.g = L.g;
     al.alpha = sign * op_scale(L);
     al.beta = beta;
+    al.ws = B->apply_ws;
     CHECK(launch_apply<double>(al, x + B->off[i], y + B->off[i], z ? z + B->off[i] : nullptr, B->stream));
   }
   return GMG_OK;
@@ -303,6 +308,11 @@ int gmg_batch_create(const gmg_desc* desc, int n_problems, const int* n_cells, g
   for (double** v : sc)
     if ((st = balloc(B, (void**)v, n_problems * 8))) return fail(st);
   if ((st = balloc(B, (void**)&B->active, n_problems * sizeof(int)))) return fail(st);
+  if (staged_apply_preferred(desc->dim, desc->degree)) {
+    long long lmax = 0;
+    for (long long l : B->len) lmax = std::max(lmax, l);
+    if (balloc(B, &B->apply_ws, 4 * lmax * 8) != GMG_OK) B->apply_ws = nullptr;
+  }
   std::vector<long long> cstart;
   std::vector<int> clen, cowner, cbegin;
   for (int i = 0; i < n_problems; ++i) {
