@@ -268,8 +268,9 @@ struct FaceSweepArgs {
 // mbarrier (bounded wait; an expired wait sets err and the kernel carries
 // on).  With NBUF = 2 the next group streams in while the current one is
 // computed.  Stages: r = sb b - (face contributions) per interior x line,
-// forward FD x | forward FD y | forward FD z, times the FD diagonal |
-// backward FD z | backward FD y | backward FD x + scatter
+// forward FD x | forward FD y | forward FD z, times the FD diagonal,
+// backward FD z (one z line per thread) | backward FD y | backward FD x +
+// scatter
 // u = omega d + (1 - omega) u_old.
 template <int K, int NT, int PPC, int NBUF>
 __global__ void __launch_bounds__(NT) patch_face_kernel(const __grid_constant__ FaceSweepArgs fa,
@@ -417,14 +418,9 @@ __global__ void __launch_bounds__(NT) patch_face_kernel(const __grid_constant__ 
       fd_smem_line<K, true>(WB + q * Z::WB + (l % M) + (l / M) * M * M, M);
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // forward z, diagonal
+    for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // forward z, diagonal, backward z
       const int q = idx / LINES, l = idx % LINES;
-      fd_smem_line<K, true, true>(WB + q * Z::WB + l, M * M, fa.dinv + l, M * M);
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // backward z
-      const int q = idx / LINES, l = idx % LINES;
-      fd_smem_line<K, false>(WB + q * Z::WB + l, M * M);
+      fd_smem_line_solve<K>(WB + q * Z::WB + l, M * M, fa.dinv + l, M * M);
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // backward y

@@ -150,6 +150,23 @@ __device__ __forceinline__ void fd_smem_line(T* base, int s, const T* __restrict
   for (int j = 0; j < M; ++j) base[j * s] = SCALE ? out[j] * __ldg(d + j * ds) : out[j];
 }
 
+// The innermost transform pair of the FD solve on one shared-memory line
+// (stride s) in registers: forward transform, times the diagonal d[0], d[ds],
+// ..., backward transform.
+template <int K>
+__device__ __forceinline__ void fd_smem_line_solve(T* base, int s, const T* __restrict__ d, int ds) {
+  constexpr int M = 2 * K - 1;
+  T v[M], w[M];
+#pragma unroll
+  for (int j = 0; j < M; ++j) v[j] = base[j * s];
+  fd_forward<K>(v, w);
+#pragma unroll
+  for (int j = 0; j < M; ++j) w[j] *= __ldg(d + j * ds);
+  fd_backward<K>(w, v);
+#pragma unroll
+  for (int j = 0; j < M; ++j) base[j * s] = v[j];
+}
+
 // Asynchronous global -> shared copy of one element (cp.async, cached in L1),
 // and the group commit / wait of the copies issued by this thread.
 __device__ __forceinline__ void async_copy(T* smem_dst, const T* gmem_src) {
@@ -206,8 +223,9 @@ struct TmaMaps<0> {};
 // origin rounded down to 16 bytes and the shift is kept per patch) or one
 // cp.async per element (ME = 0).  Stages (3D; 2D drops the z stages):
 //   z: P,Q | y: A1,A2 | x: r + forward FD along x | forward FD y |
-//   forward FD z, times the FD diagonal | backward FD z | backward FD y |
-//   backward FD x + scatter (u_new = u_old + omega d, u_old from the buffer)
+//   forward FD z, times the FD diagonal, backward FD z (one z line per
+//   thread) | backward FD y | backward FD x + scatter (u_new = u_old +
+//   omega d, u_old from the buffer)
 // Same-colour patches never write each other's closure, so the buffered
 // closure values are the values the gather (eq. "gather") reads.
 template <int DIM, int K, int NT, int PPC, int NBUF, int ME>
@@ -512,14 +530,9 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
         fd_smem_line<K, true>(WB + q * Z::WB + (l % M) + (l / M) * M * M, M);
       }
       __syncthreads();
-      for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // forward z, diagonal
+      for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // forward z, diagonal, backward z
         const int q = idx / LINES, l = idx % LINES;
-        fd_smem_line<K, true, true>(WB + q * Z::WB + l, M * M, dinv + l, M * M);
-      }
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // backward z
-        const int q = idx / LINES, l = idx % LINES;
-        fd_smem_line<K, false>(WB + q * Z::WB + l, M * M);
+        fd_smem_line_solve<K>(WB + q * Z::WB + l, M * M, dinv + l, M * M);
       }
       __syncthreads();
       for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // backward y
@@ -528,14 +541,9 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
       }
       __syncthreads();
     } else {
-      for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // forward y, diagonal
+      for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // forward y, diagonal, backward y
         const int q = idx / LINES, l = idx % LINES;
-        fd_smem_line<K, true, true>(WB + q * Z::WB + l, M, dinv + l, M);
-      }
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // backward y
-        const int q = idx / LINES, l = idx % LINES;
-        fd_smem_line<K, false>(WB + q * Z::WB + l, M);
+        fd_smem_line_solve<K>(WB + q * Z::WB + l, M, dinv + l, M);
       }
       __syncthreads();
     }
