@@ -43,9 +43,9 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 # The FP64 sweep runs each colour as two launches, the face kernel and the
 # patch kernel (shared-face form); "per launch" figures below are per colour
 # step (both kernels).  DRAM bytes of one average colour step at this
-# workload, from ncu over every launch of 5 sweeps (dram__bytes_read.sum +
-# dram__bytes_write.sum: 18,621.4 MB / 40 colour steps)
-TRAFFIC_PER_LAUNCH = (6150.6e6 + 668.1e6 + 8965.3e6 + 2837.4e6) / 40
+# workload, from ncu over every launch of 5 sweeps of the current kernels
+# (dram__bytes_read.sum + dram__bytes_write.sum: 18,627.3 MB / 40 colour steps)
+TRAFFIC_PER_LAUNCH = (6166.0e6 + 685.0e6 + 8954.5e6 + 2821.8e6) / 40
 # FP64 operations the kernels execute per patch (ncu SASS thread-instruction
 # counts of the 29,791-patch colour 0, per patch: face kernel 3,925.7 DFMA;
 # patch kernel 9,506 DFMA, 1,960 DADD, 686 DMUL)
