@@ -461,7 +461,8 @@ struct FaceSweepCfg {
   static constexpr int NBUF = K <= 4 || K == 7 ? 2 : 1;
   static constexpr int SMEM = PPC * FaceSweepSmem<K>::per_patch(NBUF) * (int)sizeof(T) + 128;
   static_assert(SMEM <= 227 * 1024, "shared-face sweep exceeds the shared memory of a CTA");
-  static_assert(PPC * (2 * K - 1) * (2 * K - 1) <= NT + 32 * 2, "lines per stage well above the threads");
+  static_assert(PPC * (2 * K - 1) * (2 * K - 1) <= NT + 32 * 2,
+                "the interior lines of a patch group should take about one pass of the CTA's threads");
 };
 constexpr int kFaceThreads = 128;
 
