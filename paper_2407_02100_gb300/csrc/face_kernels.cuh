@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(NT) face_kernel(const T* __restrict__ u, T* __
   }
 }
 
-// Shared-memory plan of the shared-face sweep, per patch (doubles):
+// Shared-memory plan of the shared-face sweep, per patch (elements of T):
 //   IN (NBUF copies): interior rows of b (TMA box rows of XB, as in the
 //       closure kernel), then the face blocks X0 X1 Y0 Y1 Z0 Z1 of the patch
 //       (two M x M fields each, padded to 16 bytes, copied by
