@@ -66,6 +66,23 @@ def test_null_problem_is_rejected(gmg):
     assert L.gmg_smooth(None, 0, None, None, 1, 0) == -1
     assert L.gmg_vcycle(None, None, None) == -1
     assert L.gmg_destroy(None) == 0
+    assert L.gmg_set_shared_faces(None, 1) == -1
+    assert L.gmg_shared_faces(None) == -1
+    assert L.gmg_set_three_pass_operator(None, 1) == -1
+    assert L.gmg_three_pass_operator(None) == -1
+
+
+def test_header_is_plain_c():
+    """The boundary header compiles as strict C99 (no C++ constructs)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = '#include "include/gmg.h"\nint main(void) { return 0; }\n'
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                        "-I", ROOT, "-x", "c", "-"], input=src, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
 
 
 def test_q1_patch_closed_form(gmg):
