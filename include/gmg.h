@@ -388,9 +388,11 @@ int gmg_set_shared_faces(gmg_problem* p, int enable);
 int gmg_shared_faces(const gmg_problem* p);
 
 /* ---- Three-pass FP64 operator -------------------------------------------
- * In 3D at degree >= 3 the FP64 level operator (gmg_apply_operator(_f64),
- * the V-cycle residuals of FP64 problems and the FP64 CG of every problem)
- * runs as three passes over the level, one 1D contraction per axis with the
+ * In 3D at degree >= 3 the FP64 level operator (the stiffness operator of
+ * Sec. 2, evaluated matrix-free by sum factorisation as in App. A.1;
+ * gmg_apply_operator(_f64), the V-cycle residuals of FP64 problems and the
+ * FP64 CG of every problem) runs as three passes over the level, one 1D
+ * contraction per axis with the
  * global 1D mass and stiffness matrices (z, then y, then x), through four
  * workspace vectors of the finest level (FP64, allocated by gmg_create).
  * Every output row is evaluated once; the tile kernel recomputes a halo of
