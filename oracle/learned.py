@@ -10,6 +10,12 @@ Model (a two-layer perceptron, our design; the paper has none):
 Loss per sample: ||d - d_exact||^2 / ||d_exact||^2, averaged over the batch,
 with d_exact the exact solve with the normalised patch matrix; DFD holds the
 damped FD term theta Ahat^{-1} r.
+
+Pinned (tests/test_oracle_varcoef.py): the analytic gradients against finite
+differences of the loss; the output layout and the loss's units by the
+full-rank eigen-correction (loss exactly zero) and by rank-r truncations
+(per eigenvector residual the loss is zero for a kept mode and s_q^2/||DEX||^2
+for a dropped one).
 """
 import numpy as np
 

@@ -21,6 +21,12 @@ with three local solvers:
               i.e. damped FD).
 Coarse levels use the geometric mean of the 2^d children as cell coefficient
 (our reading; the paper's test problem has constant coefficients).
+
+Pinned (tests/test_oracle_varcoef.py): the exact mode against Algorithm 1
+with the assembled variable matrix; fd_mean against the Poisson smoother for
+constant coefficients and by its spectral bound; the learned mode by the
+full-rank correction Ahat(w)^{-1} - theta Ahat^{-1}, with which it must
+reproduce the exact mode (2D and 3D, several h).
 """
 import itertools
 
