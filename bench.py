@@ -10,9 +10,15 @@ preconditioned CG from u = 0 to ||r|| <= 1e-10 ||b||.
 
 Reported: whole-job solve throughput (all nodes / time to 1e-10) as
 `value`; the finest-level smoother sweep rate and its roofline against the
-FP64 arithmetic peak; the same solve end to end through the C ABI with
-host buffers (`e2e`); the FP64 oracle timed on the host cores on a bounded
-sample (`cpu_baseline`).  `--impl reference` times the oracle alone.
+FP64 FMA peak measured in the same run; the same solve end to end through
+the C ABI with host buffers (`e2e`); the FP32-mixed solve of the same
+workload; the FP64 oracle's sweep of the full 64^3 grid timed on the host
+cores at one core and at all cores (`cpu_baseline`); and two further
+workloads of the paper's method, each timed once after a warm-up:
+`c3` (3D Q7 48^3, FP64 against FP32 and tensor-core smoothers inside FP64
+CG) and `c5` (3D Q3 64^3 variable coefficient, damped mean-coefficient FD
+against the learned correction, FP64 and FP32).  `--impl reference` times
+the oracle's PCG alone on a bounded sample.
 
 Multi-GPU (torchrun, one rank per GPU): the problem does not shard, so
 every rank solves an independent replica with its own seed (replicas only,
@@ -38,8 +44,9 @@ RTOL = 1e-10
 FLOP_PER_PATCH = 8 * 7 * 625 * 2 + 6 * 2401 * 2
 # minimum HBM traffic of a sweep: read b, read u, write u (8 bytes each) per node
 BYTES_PER_NODE = 24
-# FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+# FP64 peak from unit counts and clock (152 SMs x 2 DFMA/clk x 2 flop x
+# 2.07 GHz), used only if the in-run measurement (gmg_fma_peak) fails
+FP64_PEAK_DERIVED_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 # The FP64 sweep runs each colour as two launches, the face kernel and the
 # patch kernel (shared-face form); "per launch" figures below are per colour
 # step (both kernels).  DRAM bytes of one average colour step at this
@@ -48,12 +55,17 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 TRAFFIC_PER_LAUNCH = (6166.0e6 + 685.0e6 + 8954.5e6 + 2821.8e6) / 40
 # FP64 operations the kernels execute per patch (ncu SASS thread-instruction
 # counts of the 29,791-patch colour 0, per patch: face kernel 3,925.7 DFMA;
-# patch kernel 9,506 DFMA, 1,960 DADD, 686 DMUL)
+# patch kernel 9,506 DFMA, 1,960 DADD, 686 DMUL; profiles/face_sweep_fp64_q4_64.md)
 EXECUTED_FLOP_PER_PATCH = 2 * (3925.7 + 9506) + 1960 + 686
+EXECUTED_SOURCE = "profiles/face_sweep_fp64_q4_64.md (ncu SASS FP64 instruction counts, colour 0)"
 # FP64 pipe activity of the two kernels (ncu, one colour step each, current
 # kernels)
 FP64_PIPE_ACTIVE = {"face_kernel": 0.805, "patch_face_kernel": 0.811}
 CPU_SAMPLE = dict(dim=3, degree=4, n_cells=8, n_levels=3)
+BLAS_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
+# further workloads of the method, measured in the same run (one timed solve each)
+C3 = dict(dim=3, degree=7, n_cells=48, seed=0, dist="normal")
+C5 = dict(dim=3, degree=3, n_cells=64, seed=0, sigma=1.0, corr_len=0.1, samples=200000, steps=400)
 WORKLOAD = ("3D Poisson Q4, 64^3 cells, FP64 GMG(V(1,1), 8-colour vertex-patch smoother) "
             "preconditioned CG to 1e-10")
 
@@ -170,6 +182,75 @@ def cpu_sample_text():
             "same V(1,1) 8-colour patch smoother (dense LU patch solves), seed 0 U[-1,1]")
 
 
+def oracle_sweep_child(threads):
+    """One oracle sweep (Algorithm 4, dense LU patch solves, patch-local
+    blocks) of the full benchmark grid, 3D Q4 64^3, from u = 0 with the
+    bench's right-hand side; run in a fresh process whose BLAS thread count
+    the parent fixed.  Prints seconds per colour and per sweep as JSON."""
+    import numpy as np
+    from oracle.mesh import Mesh
+    from oracle.smoother import PatchSmoother
+    from paper_2407_02100_gb300 import inputs
+    m = Mesh(DIM, DEGREE, N_CELLS)
+    sm = PatchSmoother(m)
+    b = inputs.random_nodal(DIM, DEGREE, N_CELLS, 0, "uniform")
+    u = np.zeros_like(b)
+    per = []
+    t_all = time.perf_counter()
+    for c in sm.colour_order(False):
+        t0 = time.perf_counter()
+        sm.colour_step(u, b, c)
+        per.append(time.perf_counter() - t0)
+    total = time.perf_counter() - t_all
+    print(json.dumps({"threads": threads, "seconds_per_sweep": total, "seconds_per_colour": per,
+                      "nodes": m.n_nodes}), flush=True)
+    return 0
+
+
+def time_oracle_sweep(threads):
+    """Runs oracle_sweep_child in a fresh interpreter with `threads` BLAS
+    threads (set before numpy loads); returns its JSON record or None."""
+    env = dict(os.environ)
+    for v in BLAS_THREAD_VARS:
+        env[v] = str(threads)
+    try:
+        res = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sweep-child",
+                              "--threads", str(threads)], env=env, capture_output=True, text=True,
+                             timeout=600)
+    except subprocess.TimeoutExpired:
+        return None
+    for ln in res.stdout.splitlines()[::-1]:
+        if ln.startswith("{"):
+            return json.loads(ln)
+    return None
+
+
+def cpu_baseline_record(gpu_sweep_mdofs):
+    """The oracle's sweep of the full benchmark grid at one core and at all
+    cores (BLAS threads; the gather is plain NumPy indexing), and the oracle
+    PCG on the bounded 8^3 sample for the solve metric."""
+    nproc = os.cpu_count() or 1
+    one = time_oracle_sweep(1)
+    allc = time_oracle_sweep(nproc)
+    rec = {"kind": "oracle", "unit": "MDoF/s (one smoother sweep, all nodes)"}
+    if allc:
+        rec.update({"value": allc["nodes"] / allc["seconds_per_sweep"] / 1e6, "cores": nproc,
+                    "seconds_per_sweep": allc["seconds_per_sweep"]})
+    if one:
+        rec["single_core"] = {"value": one["nodes"] / one["seconds_per_sweep"] / 1e6, "cores": 1,
+                              "seconds_per_sweep": one["seconds_per_sweep"]}
+    rec["sample"] = ("oracle smoother sweep (Algorithm 4, ascending colours, dense LU patch solves "
+                     "from patch-local blocks) of the full 3D Q4 64^3 grid (16,974,593 nodes, "
+                     "250,047 patches), u = 0, the bench's seed-0 U[-1,1] right-hand side; "
+                     f"nproc = {nproc}; cores = BLAS threads allowed")
+    if "value" in rec and gpu_sweep_mdofs:
+        rec["gpu_sweep_over_oracle"] = gpu_sweep_mdofs / rec["value"]
+    v, dt, its = time_oracle_solve(1)
+    rec["pcg_sample"] = {"value": v, "unit": "MDoF/s (all nodes / GMG-CG time to 1e-10)", "cores": nproc,
+                         "sample": cpu_sample_text() + f"; {dt:.2f} s per solve, {its} iterations"}
+    return rec
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -266,17 +347,28 @@ def run_ours(args):
         gmg.gmg_smooth(P.h, P.finest, us, b, 1, False)
     torch.cuda.synchronize()
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s0.record(stream)
-    for _ in range(n_sweeps):
-        gmg.gmg_smooth(P.h, P.finest, us, b, 1, False)
-    s1.record(stream)
-    torch.cuda.synchronize()
+    with ClockSampler(local) as sweep_clocks:
+        s0.record(stream)
+        for _ in range(n_sweeps):
+            gmg.gmg_smooth(P.h, P.finest, us, b, 1, False)
+        s1.record(stream)
+        torch.cuda.synchronize()
     sweep_s = s0.elapsed_time(s1) * 1e-3 / n_sweeps
     patches = (N_CELLS - 1) ** DIM
     flops_sweep = FLOP_PER_PATCH * patches
-    achieved_tflops = flops_sweep / sweep_s / 1e12
+    method_tflops = flops_sweep / sweep_s / 1e12
     executed_tflops = EXECUTED_FLOP_PER_PATCH * patches / sweep_s / 1e12
     hbm_gbs = BYTES_PER_NODE * nodes / sweep_s / 1e9
+
+    # ---- measured FMA peaks of this GPU (roofline denominators) ----
+    try:
+        peak64, peak64_src = gmg.gmg_fma_peak(gmg.GMG_FP64), "measured in this run: gmg_fma_peak(GMG_FP64)"
+    except gmg.GmgError:
+        peak64, peak64_src = FP64_PEAK_DERIVED_TFLOPS, "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz"
+    try:
+        peak32 = gmg.gmg_fma_peak(gmg.GMG_FP32)
+    except gmg.GmgError:
+        peak32 = None
 
     # ---- end to end through the C ABI with host buffers ----
     b_pin = torch.empty(n_elems, dtype=torch.float64, pin_memory=True)
@@ -302,6 +394,14 @@ def run_ours(args):
     gmg.gmg_apply_operator_f64(P.h, P.finest, u, r)
     rel_res = float(torch.linalg.vector_norm(b - r) / torch.linalg.vector_norm(b))
 
+    # ---- per-phase times of one FP64 solve (events per phase, no graph) ----
+    gmg.gmg_set_phase_timing(P.h, True)
+    up = P.zeros(dtype=torch.float64)
+    _, st_ph = gmg.cg_gmg_solve(P.h, up, b, RTOL, 100)
+    gmg.gmg_set_phase_timing(P.h, False)
+    phases = gmg.phase_times(st_ph)
+    del up
+
     # ---- mixed precision: FP32 smoother / V-cycle inside the FP64 CG, same
     # workload, same accuracy target ----
     P32 = gmg.Problem(DIM, DEGREE, N_CELLS, n_levels=0, precision=gmg.GMG_FP32)
@@ -312,12 +412,13 @@ def run_ours(args):
         _, st32 = gmg.cg_gmg_solve(P32.h, u32, b, RTOL, 100)
     torch.cuda.synchronize()
     m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    m0.record(stream)
-    for _ in range(args.steps):
-        u32.zero_()
-        _, st32 = gmg.cg_gmg_solve(P32.h, u32, b, RTOL, 100)
-    m1.record(stream)
-    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks32:
+        m0.record(stream)
+        for _ in range(args.steps):
+            u32.zero_()
+            _, st32 = gmg.cg_gmg_solve(P32.h, u32, b, RTOL, 100)
+        m1.record(stream)
+        torch.cuda.synchronize()
     ms32 = m0.elapsed_time(m1) / args.steps
     diff32 = float(torch.linalg.vector_norm(u32 - u) / torch.linalg.vector_norm(u))
     gmg.gmg_apply_operator_f64(P32.h, P32.finest, u32, r)
@@ -334,9 +435,21 @@ def run_ours(args):
     torch.cuda.synchronize()
     sweep32_s = s0.elapsed_time(s1) * 1e-3 / n_sweeps
     P32.close()
+    del us32, bs32, u32
+
+    extra = {}
+    if not args.no_extra and ws == 1:
+        P.close()
+        del us, r, b_e2e
+        torch.cuda.empty_cache()
+        extra["c3"] = c3_leg(gmg, inputs, torch, local)
+        torch.cuda.empty_cache()
+        extra["c5"] = c5_leg(gmg, inputs, torch, local)
+        torch.cuda.empty_cache()
+    else:
+        P.close()
 
     if rank != 0:
-        P.close()
         if dist is not None:
             dist.barrier()
             dist.destroy_process_group()
@@ -344,9 +457,7 @@ def run_ours(args):
 
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        v, dt, its = time_oracle_solve(1)
-        cpu = {"value": v, "unit": "MDoF/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": cpu_sample_text() + f"; {dt:.2f} s per solve, {its} iterations"}
+        cpu = cpu_baseline_record(nodes / sweep_s / 1e6)
 
     line = {
         "metric": METRIC,
@@ -367,46 +478,162 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (u, b: 136 MB each)",
                    "cg_iterations": iters[-1], "final_rel_residual": rel_res},
         "time_to_solution_ms": ms_per_step,
+        "phase_ms": phases,
         "smoother": {"ms_per_sweep": sweep_s * 1e3, "mdofs": nodes / sweep_s / 1e6,
                      "hbm_gbs_algorithmic": hbm_gbs, "patches": patches,
-                     "flop_per_patch": FLOP_PER_PATCH},
+                     "flop_per_patch": FLOP_PER_PATCH, "clocks": sweep_clocks.summary()},
         "fp32_mixed": {"time_to_solution_ms": ms32, "mdofs": nodes / (ms32 * 1e-3) / 1e6,
                        "cg_iterations": st32.iterations, "final_rel_residual": res32,
                        "rel_diff_vs_fp64_solution": diff32,
                        "speedup_vs_fp64": ms_per_step / ms32,
                        "smoother_ms_per_sweep": sweep32_s * 1e3,
                        "smoother_mdofs": nodes / sweep32_s / 1e6,
-                       "smoother_hbm_gbs_algorithmic": 12 * nodes / sweep32_s / 1e9},
-        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+                       "smoother_hbm_gbs_algorithmic": 12 * nodes / sweep32_s / 1e9,
+                       "smoother_work_equivalent_tflops": flops_sweep / sweep32_s / 1e12,
+                       "smoother_work_equivalent_frac_of_fp32_peak":
+                           (flops_sweep / sweep32_s / 1e12 / peak32) if peak32 else None,
+                       "fp32_fma_peak_tflops": peak32,
+                       "clocks": clocks32.summary()},
+        "roofline": {"bound": "alu", "achieved": executed_tflops, "peak": peak64,
+                     "unit": "TFLOP/s", "frac": executed_tflops / peak64,
+                     "peak_source": peak64_src + " (of measured)",
                      "traffic": TRAFFIC_PER_LAUNCH,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum over every "
-                                       "launch of 5 sweeps, per colour step (face kernel + patch kernel)",
+                                       "launch of 5 sweeps, per colour step (face kernel + patch kernel); "
+                                       "profiles/sweep_dram_bytes_per_dof_q4_64.md",
                      "algorithmic_bytes_per_launch": BYTES_PER_NODE * nodes / 8,
                      "executed_flop_per_patch": EXECUTED_FLOP_PER_PATCH,
-                     "executed_tflops": executed_tflops,
-                     "executed_frac": executed_tflops / FP64_PEAK_TFLOPS,
+                     "executed_source": EXECUTED_SOURCE,
+                     "work_equivalent": {"achieved": method_tflops, "frac": method_tflops / peak64,
+                                         "flop_per_patch": FLOP_PER_PATCH,
+                                         "note": "the method's operation count (2^3 cells x 7 contractions "
+                                                 "of (k+1)^4 + 6 FD contractions of (2k-1)^4 multiply-adds); "
+                                                 "the kernels compute the same sweep with fewer operations "
+                                                 "(banded two-cell matrices, even/odd FD, residual from the "
+                                                 "closure faces), so this rate exceeds the peak"},
                      "fp64_pipe_active_ncu": FP64_PIPE_ACTIVE,
                      "kernel": "face_kernel<4,128> + patch_face_kernel<4,256,5,2> (FP64 shared-face "
-                               "sweep), one pair of launches per colour; timed as whole sweeps",
-                     "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz",
-                     "note": "achieved and frac count the method's operation count (98,812 flop per "
-                             "patch); the kernels execute 29,510 FP64 flop per patch (banded two-cell "
-                             "matrices, even/odd FD, residual from the closure faces, each face "
-                             "evaluated once per colour), so frac > 1; executed_frac and the FP64 "
-                             "pipe activity are the utilisation of the hardware"},
+                               "sweep), one pair of launches per colour; timed as whole sweeps"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "MDoF/s", "h2d_bytes_per_step": n_elems * 8,
                 "d2h_bytes_per_step": n_elems * 8},
         "gpu_launches": launches,
         "clocks": clocks.summary(),
     }
+    line.update(extra)
     print(json.dumps(line), flush=True)
-    P.close()
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def timed_solve(gmg, torch, P, u, b, local, max_it=300):
+    """One warm-up solve, then one timed solve (CUDA events on the current
+    stream, clocks sampled around it); returns (ms, stats, status, clocks)."""
+    u.zero_()
+    gmg.cg_gmg_solve(P.h, u, b, RTOL, max_it, raise_on_error=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    with ClockSampler(local) as ck:
+        u.zero_()
+        e0.record(stream)
+        status, st = gmg.cg_gmg_solve(P.h, u, b, RTOL, max_it, raise_on_error=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    return e0.elapsed_time(e1), st, status, ck.summary()
+
+
+def rel_diff(torch, a, b):
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
+def c3_leg(gmg, inputs, torch, local):
+    """3D Poisson Q7 48^3 (38,272,753 nodes), N(0,1) RHS: the FP64 solve
+    against FP32 (FFMA) and 3xTF32 tensor-core smoothers inside the same FP64
+    CG, time to 1e-10 and the difference to the FP64 solution."""
+    c = C3
+    rhs = inputs.random_nodal(c["dim"], c["degree"], c["n_cells"], c["seed"], c["dist"])
+    nodes = (c["n_cells"] * c["degree"] + 1) ** c["dim"]
+    out = {"workload": "3D Poisson Q7, 48^3 cells, N(0,1) RHS, GMG(V(1,1))-PCG to 1e-10",
+           "nodes": nodes}
+    ref = None
+    for name, prec in (("fp64", gmg.GMG_FP64), ("fp32_mixed", gmg.GMG_FP32),
+                       ("fp32_tc_mixed", gmg.GMG_FP32_TC)):
+        P = gmg.Problem(c["dim"], c["degree"], c["n_cells"], precision=prec)
+        b = P.to_device(rhs, dtype=torch.float64)
+        u = P.zeros(dtype=torch.float64)
+        ms, st, status, ck = timed_solve(gmg, torch, P, u, b, local)
+        rec = {"time_to_solution_ms": ms, "mdofs": nodes / ms * 1e3 / 1e6, "iterations": st.iterations,
+               "rel_residual": st.relative_residual, "status": gmg.STATUS.get(status, status), "clocks": ck}
+        if ref is None:
+            ref = u.clone()
+        else:
+            rec["rel_diff_vs_fp64_solution"] = rel_diff(torch, u, ref)
+        out[name] = rec
+        P.close()
+        del u, b
+    for name in ("fp32_mixed", "fp32_tc_mixed"):
+        out[name]["speedup_vs_fp64"] = out["fp64"]["time_to_solution_ms"] / out[name]["time_to_solution_ms"]
+    return out
+
+
+def c5_leg(gmg, inputs, torch, local):
+    """3D variable coefficient -div(a grad u) = f, Q3 64^3, a = exp(g), g a
+    Gaussian random field (sigma 1, correlation length 0.1): damped
+    mean-coefficient FD against the learned correction (trained in this run
+    on exact patch solves), FP64 and FP32 smoothers inside FP64 CG."""
+    import numpy as np
+    c = C5
+    dim, k, n = c["dim"], c["degree"], c["n_cells"]
+    coef = inputs.lognormal_coefficient(dim, n, c["seed"], c["sigma"], c["corr_len"])
+    rhs = inputs.random_nodal(dim, k, n, c["seed"] + 1)
+    nodes = (n * k + 1) ** dim
+    nint = (2 * k - 1) ** dim
+    out = {"workload": "3D -div(a grad u) = f, Q3, 64^3 cells, a = exp(GRF sigma 1, l 0.1), N(0,1) RHS, "
+                       "GMG(V(1,1))-PCG to 1e-10",
+           "nodes": nodes, "coef_contrast": float(coef.max() / coef.min()), "samples": None}
+    ref = None
+    for pname, prec in (("fp64", gmg.GMG_FP64), ("fp32", gmg.GMG_FP32)):
+        for mode in ("fd_mean", "learned"):
+            P = gmg.Problem(dim, k, n, precision=prec)
+            gmg.gmg_set_coefficient(P.h, coef)
+            rec = {}
+            if mode == "learned":
+                nfine = (n - 1) ** dim
+                total = gmg.learned_patch_count(dim, n, P.n_levels)
+                rng = np.random.default_rng(c["seed"] + 2)
+                nf = max(0, min(nfine, c["samples"] - (total - nfine)))
+                verts = rng.permutation(np.concatenate([rng.permutation(nfine)[:nf], np.arange(nfine, total)]))
+                res = torch.tensor(np.random.default_rng(c["seed"] + 3).standard_normal((len(verts), nint)),
+                                   device="cuda")
+                out["samples"] = len(verts)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                hist, kept = gmg.gmg_learned_train(P.h, verts, res, steps=c["steps"], batch=4096, lr=3e-3,
+                                                   seed=c["seed"])
+                torch.cuda.synchronize()
+                rec.update({"train_s": time.perf_counter() - t0, "loss_first": hist[0], "loss_last": hist[-1],
+                            "kept_patches": kept})
+                del res
+            b = P.to_device(rhs, dtype=torch.float64)
+            u = P.zeros(dtype=torch.float64)
+            ms, st, status, ck = timed_solve(gmg, torch, P, u, b, local)
+            rec.update({"time_to_solution_ms": ms, "iterations": st.iterations,
+                        "rel_residual": st.relative_residual, "status": gmg.STATUS.get(status, status),
+                        "clocks": ck})
+            if ref is None:
+                ref = u.clone()
+            else:
+                rec["rel_diff_vs_fp64_fd_mean_solution"] = rel_diff(torch, u, ref)
+            out[f"{pname}_{mode}"] = rec
+            P.close()
+            del u, b
+    base = out["fp64_fd_mean"]["time_to_solution_ms"]
+    for key in ("fp64_learned", "fp32_fd_mean", "fp32_learned"):
+        out[key]["speedup_vs_fp64_fd_mean"] = base / out[key]["time_to_solution_ms"]
+    return out
 
 
 def main():
@@ -418,7 +645,12 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--sweeps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the C3 and C5 legs")
+    ap.add_argument("--oracle-sweep-child", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--threads", type=int, default=1, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_sweep_child:
+        return oracle_sweep_child(args.threads)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

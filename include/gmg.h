@@ -88,6 +88,18 @@ typedef struct {
   void* stream;     /* cudaStream_t used by every call on this problem */
 } gmg_desc;
 
+/* Phases of a solve, as timed by gmg_set_phase_timing (the GPU form of the
+ * breakdown of a V-cycle's time into its parts, Sec. 4). */
+enum gmg_phase {
+  GMG_PHASE_SMOOTH = 0,    /* patch smoothing sweeps of every level */
+  GMG_PHASE_OPERATOR = 1,  /* level residuals b - A x and the CG's operator */
+  GMG_PHASE_TRANSFER = 2,  /* restriction and prolongation */
+  GMG_PHASE_COARSE = 3,    /* coarsest-level solve */
+  GMG_PHASE_VECTOR = 4,    /* CG dot products and updates, precision
+                              conversions, zeroing of level corrections */
+  GMG_PHASE_COUNT = 5
+};
+
 typedef struct {
   int iterations;            /* CG iterations done */
   int converged;             /* 1 if ||r|| <= rtol ||b|| */
@@ -95,6 +107,9 @@ typedef struct {
   double final_residual;     /* ||b - A u|| (recurrence residual) */
   double relative_residual;  /* final_residual / ||b|| */
   double residual_history[64]; /* relative residuals, entry i after iteration i */
+  double phase_ms[GMG_PHASE_COUNT]; /* GPU milliseconds per phase (enum
+                                       gmg_phase) when phase timing is on,
+                                       zeros otherwise */
 } gmg_solve_stats;
 
 /* Create a problem: builds the level hierarchy (Sec. 2, nested meshes), the
@@ -194,6 +209,15 @@ int gmg_vcycle(gmg_problem* p, void* x, const void* b);
 int cg_gmg_solve(gmg_problem* p, double* u, const double* b, double rtol, int max_it,
                  gmg_solve_stats* stats);
 
+/* Per-phase timing of cg_gmg_solve (enable != 0) or none (0, the default).
+ * When on, the solver records a pair of CUDA events on the problem's stream
+ * around each phase (enum gmg_phase) of every iteration, launches each
+ * iteration's kernels directly instead of replaying its CUDA graph, and
+ * returns the summed event times in gmg_solve_stats.phase_ms.  Results are
+ * the same either way; the events and the direct launches add a little
+ * time.  GMG_ERR_INVALID_ARG for a null problem. */
+int gmg_set_phase_timing(gmg_problem* p, int enable);
+
 /* gmg_smooth without a problem object and without allocating device memory
  * (the paper has no counterpart: this is a deployment variant).  For callers
  * that cannot call cudaMalloc -- their device memory belongs to another
@@ -206,10 +230,17 @@ int cg_gmg_solve(gmg_problem* p, double* u, const double* b, double rtol, int ma
  * array of (2*8-1)^3 doubles (27 KB, kept on every GPU that loads the
  * library until exit); patches needing more are rejected with
  * GMG_ERR_INVALID_ARG, as are bad dim/degree/n_cells/damping/pointers.
- * The first call on a device looks the array's address up (once, with that
- * device current); make that first call before any stream capture.  Every
- * call rewrites the part of the array it uses; calls that overlap on the GPU
- * (different streams, no ordering between them) race on it. */
+ * SET-UP: the first call for a (device, degree) pair does that pair's set-up
+ * with the device current: it looks the array's address up and copies the
+ * degree's coefficient tables to __constant__ memory (cudaMemcpyToSymbol:
+ * synchronous, no allocation).  Make that first call outside any stream
+ * capture.  Every later call for the pair only enqueues kernels on `stream`:
+ * one that rewrites the part of the array the degree uses, then one per
+ * colour.  Calls that overlap on the GPU (different streams, no ordering
+ * between them) race on the array.
+ * STATUS: a bounded wait of the sweep kernel that expires is not reported by
+ * the return value (the call returns before the kernels run); it sets the
+ * device flag read by gmg_tc_status(). */
 int gmg_smooth_noalloc(int dim, int degree, int n_cells, double damping, double* u,
                        const double* b, int n_sweeps, int reverse, void* stream);
 
@@ -319,6 +350,22 @@ int gmg_learned_train(gmg_problem* p, int n_samples, const int* sample_vertices,
  * `count` floats. */
 int gmg_learned_corrections(const gmg_problem* p, int level, float* out, long long count);
 
+/* The training targets of gmg_learned_train, exposed for testing: for each of
+ * n patches, the exact reference-unit local solve d_exact = Ahat(w)^{-1} r and
+ * the damped fast-diagonalisation solve d_fd = theta Ahat^{-1} r, theta =
+ * min(1, 1.8 / max_c w_c) (App. A.3 for Ahat^{-1}; the exact solve is the
+ * A_j^{-1} of the local problem, Sec. 2.1, for cells of unit width).  Ahat(w)
+ * is the patch-interior stiffness block assembled from the 2^dim unit-cell
+ * matrices weighted by w, and factorised by dense FP64 Cholesky on the GPU.
+ * w: DEVICE double n x 2^dim cell weights, cell offset o_0 fastest, with
+ * geometric mean 1 per patch (the cell coefficients divided by their
+ * geometric mean); r: DEVICE double n x m^dim residuals (m = 2 degree - 1,
+ * lexicographic, x fastest); d_exact, d_fd: DEVICE double n x m^dim outputs.
+ * degree 1..3.  Allocates and frees device memory and synchronises the
+ * device.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+int gmg_exact_patch_solve(int dim, int degree, int n, const double* w, const double* r, double* d_exact,
+                          double* d_fd);
+
 /* Loss and gradient of the perceptron on one batch (for testing the kernels):
  * params (DEVICE, FP32) = W1 [hidden x 2^dim] | b1 [hidden] | W2 [no x hidden]
  * | b2 [no] with no = m^dim rank + rank; X (DEVICE FP32, n x 2^dim); R, DFD,
@@ -416,8 +463,11 @@ int gmg_three_pass_operator(const gmg_problem* p);
  * closure with one TMA box per vector when the vectors' base addresses are
  * 16-byte aligned and their pitches multiples of 16 bytes, else with one
  * cp.async per element).  An expired wait makes the kernel finish early and
- * set a device flag.  gmg_tc_status synchronises the device, returns GMG_OK
- * or the recorded status (GMG_ERR_TIMEOUT) and clears it. */
+ * set a device flag (one per device).  This covers every sweep kernel of the
+ * library (gmg_smooth and its variants, gmg_smooth_noalloc, the V-cycle and
+ * CG, batches, the variable-coefficient sweep) and the tensor-core sweep.
+ * gmg_tc_status synchronises the device, returns GMG_OK or the recorded
+ * status (GMG_ERR_TIMEOUT) of the current device and clears it. */
 int gmg_tc_status(void);
 
 /* Diagnostic of the tensor-core encoding: D = A B^T for one 128 x 16 (A) by
@@ -429,6 +479,17 @@ int gmg_tc_status(void);
  * and D still holds the product.  Allocates and frees device memory and
  * synchronises. */
 int gmg_tc_probe(const float* A, const float* B, float* D, int force_timeout);
+
+/* Diagnostic with no counterpart in the paper: the measured peak rate of the
+ * current device's fused multiply-add pipe for precision GMG_FP64 (DFMA) or
+ * GMG_FP32 (FFMA), in TFLOP/s (2 flops per FMA).  It is the denominator of
+ * the arithmetic roofline that the sweep kernels are reported against.  A
+ * grid of 1024 threads per SM runs 8 independent FMA chains per thread; the
+ * best of three timed launches after a warm-up (about 0.1 s each, CUDA
+ * events on a private non-blocking stream) is returned in *tflops.  Uses no
+ * device allocation; synchronises its stream.  Errors: INVALID_ARG (other
+ * precision, NULL tflops), CUDA. */
+int gmg_fma_peak(int precision, double* tflops);
 
 /* Number of CUDA kernels this library has enqueued since it was loaded
  * (host-side counter, all problems and devices).  Host-only. */

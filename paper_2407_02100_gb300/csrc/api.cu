@@ -35,6 +35,68 @@ void drop_cg_graph(gmg_problem* p) {
   p->cg_graph_u = nullptr;
 }
 
+static cudaEvent_t take_event(gmg_problem* p) {
+  if (!p->event_pool.empty()) {
+    cudaEvent_t e = p->event_pool.back();
+    p->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+PhaseScope::PhaseScope(gmg_problem* p, int phase) : p_(p), phase_(phase) {
+  if (!p_->phase_timing) return;
+  if (p_->phase_depth++ > 0) return;
+  start_ = take_event(p_);
+  if (start_ && cudaEventRecord(start_, p_->stream) != cudaSuccess) {
+    cudaGetLastError();
+    p_->event_pool.push_back(start_);
+    start_ = nullptr;
+  }
+}
+
+PhaseScope::~PhaseScope() {
+  if (!p_->phase_timing) return;
+  --p_->phase_depth;
+  if (!start_) return;
+  cudaEvent_t stop = take_event(p_);
+  if (stop && cudaEventRecord(stop, p_->stream) == cudaSuccess) {
+    p_->phase_marks.push_back({phase_, start_, stop});
+    return;
+  }
+  cudaGetLastError();
+  p_->event_pool.push_back(start_);
+  if (stop) p_->event_pool.push_back(stop);
+}
+
+void collect_phases(gmg_problem* p) {
+  for (const auto& m : p->phase_marks) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, m.start, m.stop) == cudaSuccess)
+      p->phase_ms[m.phase] += ms;
+    else
+      cudaGetLastError();
+    p->event_pool.push_back(m.start);
+    p->event_pool.push_back(m.stop);
+  }
+  p->phase_marks.clear();
+}
+
+void release_phase_events(gmg_problem* p) {
+  for (const auto& m : p->phase_marks) {
+    cudaEventDestroy(m.start);
+    cudaEventDestroy(m.stop);
+  }
+  p->phase_marks.clear();
+  for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
+  p->event_pool.clear();
+}
+
 int dalloc(gmg_problem* p, void** ptr, size_t bytes) {
   *ptr = nullptr;
   if (bytes == 0) bytes = 16;
@@ -82,6 +144,7 @@ bool valid_level(const gmg_problem* p, int level) {
 // ---- typed dispatch helpers ----
 int apply_level(gmg_problem* p, int level, const void* x, void* y, const void* bvec, double alpha,
                 double beta) {
+  PhaseScope ph(p, GMG_PHASE_OPERATOR);
   const Level& L = p->levels[level];
   if (p->varcoef) {
     if (p->esize == 8)
@@ -229,6 +292,7 @@ int build_slabs(gmg_problem* p, int level, int W) {
 }
 
 int smooth(gmg_problem* p, int level, void* u, const void* b, int n_sweeps, int reverse) {
+  PhaseScope ph(p, GMG_PHASE_SMOOTH);
   Level& L = p->levels[level];
   const int nc = 1 << L.g.dim;
   if (L.slab_w > 0 && !p->varcoef) {
@@ -378,6 +442,7 @@ AxisOp make_op(int axis, const Arr& in, const int in_off[3], const Arr& out, con
 
 // fine += P coarse (tensor product of the 1D embedding, one axis per pass)
 int prolongate_add(gmg_problem* p, int cl, const void* coarse, void* fine) {
+  PhaseScope ph(p, GMG_PHASE_TRANSFER);
   const LevelGeom& gc = p->levels[cl].g;
   const LevelGeom& gf = p->levels[cl + 1].g;
   const int k = gc.k, dim = gc.dim, Nc = gc.N, Nf = gf.N;
@@ -402,6 +467,7 @@ int prolongate_add(gmg_problem* p, int cl, const void* coarse, void* fine) {
 // one axis per pass; along axes already restricted only interior coarse
 // nodes are computed, stored at their lattice index.
 int restrict_to(gmg_problem* p, int fl, const void* fine, void* coarse) {
+  PhaseScope ph(p, GMG_PHASE_TRANSFER);
   const LevelGeom& gf = p->levels[fl].g;
   const LevelGeom& gc = p->levels[fl - 1].g;
   const int k = gc.k, dim = gc.dim, Nc = gc.N, Nf = gf.N;
@@ -474,6 +540,7 @@ int coarse_fd(gmg_problem* p, const void* b, void* x, const void* fwd, const voi
 }
 
 int coarse_solve(gmg_problem* p, const void* b, void* x) {
+  PhaseScope ph(p, GMG_PHASE_COARSE);
   const LevelGeom& g = p->levels[0].g;
   if (p->varcoef) {
     if (p->esize == 8)
@@ -492,7 +559,10 @@ int coarse_solve(gmg_problem* p, const void* b, void* x) {
 int vcycle_level(gmg_problem* p, int l, void* x, const void* b) {
   Level& L = p->levels[l];
   if (l == 0) return coarse_solve(p, b, x);
-  if (cudaMemsetAsync(x, 0, L.n_elems * p->esize, p->stream) != cudaSuccess) return GMG_ERR_CUDA;
+  {
+    PhaseScope ph(p, GMG_PHASE_VECTOR);
+    if (cudaMemsetAsync(x, 0, L.n_elems * p->esize, p->stream) != cudaSuccess) return GMG_ERR_CUDA;
+  }
   CHECK(smooth(p, l, x, b, p->desc.pre_sweeps, 0));
   CHECK(apply_level(p, l, x, L.r, b, -op_scale(L), 1.0));
   Level& C = p->levels[l - 1];
@@ -544,6 +614,7 @@ int gmg_destroy(gmg_problem* p) {
   if (!p) return GMG_OK;
   cudaStreamSynchronize(p->stream);
   drop_cg_graph(p);
+  release_phase_events(p);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   for (void* ptr : p->owned) cudaFree(ptr);
   delete p;
@@ -863,6 +934,12 @@ int gmg_set_local_solver(gmg_problem* p, int solver) {
   return GMG_ERR_INVALID_ARG;
 }
 
+int gmg_set_phase_timing(gmg_problem* p, int enable) {
+  if (!p) return GMG_ERR_INVALID_ARG;
+  p->phase_timing = enable != 0;
+  return GMG_OK;
+}
+
 int gmg_set_three_pass_operator(gmg_problem* p, int enable) {
   if (!p) return GMG_ERR_INVALID_ARG;
   drop_cg_graph(p);
@@ -948,23 +1025,37 @@ int cg_gmg_solve(gmg_problem* p, double* u, const double* b, double rtol, int ma
   std::memset(&local, 0, sizeof(local));
   double h_sc[S_COUNT];
   const cudaStream_t user_stream = s;
+  const bool timing = p->phase_timing;
+  p->phase_marks.clear();
+  for (double& t : p->phase_ms) t = 0.0;
   auto fetch = [&]() -> int {
     if (cudaMemcpyAsync(h_sc, sc, sizeof(h_sc), cudaMemcpyDeviceToHost, s) != cudaSuccess) return GMG_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return GMG_ERR_CUDA;
+    if (timing) collect_phases(p);
     return GMG_OK;
   };
   auto precondition = [&]() -> int {  // z = V(r)
     if (p->esize == 8) return vcycle_level(p, Lf, p->cg_z, p->cg_r);
-    CHECK(launch_convert_f64_f32(n, p->cg_r, (float*)F.b, s));
+    {
+      PhaseScope ph(p, GMG_PHASE_VECTOR);
+      CHECK(launch_convert_f64_f32(n, p->cg_r, (float*)F.b, s));
+    }
     CHECK(vcycle_level(p, Lf, F.u, F.b));
+    PhaseScope ph(p, GMG_PHASE_VECTOR);
     return launch_convert_f32_f64(n, (const float*)F.u, p->cg_z, s);
   };
   auto finish = [&](int status) -> int {
+    if (timing) {
+      if (cudaStreamSynchronize(s) == cudaSuccess) collect_phases(p);
+      cudaGetLastError();
+      for (int i = 0; i < GMG_PHASE_COUNT; ++i) local.phase_ms[i] = p->phase_ms[i];
+    }
     if (st) *st = local;
     return status;
   };
   // FP64 operator of the outer CG: y = sign A x + beta z
   auto cg_apply = [&](const double* x, double* y, const double* z, double sign, double beta) -> int {
+    PhaseScope ph(p, GMG_PHASE_OPERATOR);
     if (p->varcoef)
       return launch_apply_var<double>(F.g, F.n_elems, x, y, z, sign * op_scale(F), beta, p->coef64, s);
     ApplyLaunch al;
@@ -976,8 +1067,11 @@ int cg_gmg_solve(gmg_problem* p, double* u, const double* b, double rtol, int ma
   };
   // r = b - A u
   CHECK(cg_apply(u, p->cg_r, b, -1.0, 1.0));
-  CHECK(launch_dot(n, b, b, p->partial, sc + S_BB, s));
-  CHECK(launch_dot(n, p->cg_r, p->cg_r, p->partial, sc + S_RR, s));
+  {
+    PhaseScope ph(p, GMG_PHASE_VECTOR);
+    CHECK(launch_dot(n, b, b, p->partial, sc + S_BB, s));
+    CHECK(launch_dot(n, p->cg_r, p->cg_r, p->partial, sc + S_RR, s));
+  }
   CHECK(fetch());
   const double bnorm = std::sqrt(h_sc[S_BB]);
   double rnorm = std::sqrt(h_sc[S_RR]);
@@ -991,21 +1085,29 @@ int cg_gmg_solve(gmg_problem* p, double* u, const double* b, double rtol, int ma
     return finish(GMG_OK);
   }
   CHECK(precondition());
-  if (cudaMemcpyAsync(p->cg_p, p->cg_z, n * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-    return finish(GMG_ERR_CUDA);
-  CHECK(launch_dot(n, p->cg_r, p->cg_z, p->partial, sc + S_RZ, s));
+  {
+    PhaseScope ph(p, GMG_PHASE_VECTOR);
+    if (cudaMemcpyAsync(p->cg_p, p->cg_z, n * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return finish(GMG_ERR_CUDA);
+    CHECK(launch_dot(n, p->cg_r, p->cg_z, p->partial, sc + S_RZ, s));
+  }
   // q = A p, alpha = rz / pq, u += alpha p, r -= alpha q, rr = r.r
   auto update = [&]() -> int {
     CHECK(cg_apply(p->cg_p, p->cg_q, nullptr, 1.0, 0.0));
+    PhaseScope ph(p, GMG_PHASE_VECTOR);
     CHECK(launch_dot(n, p->cg_p, p->cg_q, p->partial, sc + S_PQ, s));
     return launch_cg_update(n, u, p->cg_r, p->cg_p, p->cg_q, sc + S_RZ, sc + S_PQ, p->partial, sc + S_RR, s);
   };
   // z = V(r), beta = rz_new / rz, p = z + beta p, then the update
   auto iteration_body = [&]() -> int {
     CHECK(precondition());
-    CHECK(launch_dot(n, p->cg_r, p->cg_z, p->partial, sc + S_RZN, s));
-    CHECK(launch_cg_direction(n, p->cg_p, p->cg_z, sc + S_RZN, sc + S_RZ, s));
-    if (cudaMemcpyAsync(sc + S_RZ, sc + S_RZN, 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return GMG_ERR_CUDA;
+    {
+      PhaseScope ph(p, GMG_PHASE_VECTOR);
+      CHECK(launch_dot(n, p->cg_r, p->cg_z, p->partial, sc + S_RZN, s));
+      CHECK(launch_cg_direction(n, p->cg_p, p->cg_z, sc + S_RZN, sc + S_RZ, s));
+      if (cudaMemcpyAsync(sc + S_RZ, sc + S_RZN, 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return GMG_ERR_CUDA;
+    }
     return update();
   };
   CHECK(update());
@@ -1024,6 +1126,10 @@ int cg_gmg_solve(gmg_problem* p, double* u, const double* b, double rtol, int ma
       return finish(GMG_OK);
     }
     if (it == max_it) break;
+    if (timing) {  // direct launches, so that every phase gets its events
+      CHECK(iteration_body());
+      continue;
+    }
     // next iteration up to its convergence check: a CUDA graph replay
     // (captured once the first iteration has prepared every kernel)
     if (!p->cg_exec || p->cg_graph_u != u) {

@@ -492,7 +492,10 @@ static int face_sweep_impl(const PatchLaunch& pl, T* u, const T* b, const T* din
   using Z = FaceSweepSmem<K>;
   auto fk = face_kernel<K, kFaceThreads>;
   auto pk = patch_face_kernel<K, SC::NT, SC::PPC, SC::NBUF>;
-  static int per_sm = 0;
+  static PerDevice<int> per_sm_dev;
+  int* const per_sm_p = per_sm_dev.get();
+  if (!per_sm_p) return GMG_ERR_CUDA;
+  int& per_sm = *per_sm_p;
   if (per_sm == 0) {
     if (prepare(fk, FC::SMEM) != GMG_OK || prepare(pk, SC::SMEM) != GMG_OK) return GMG_ERR_CUDA;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pk, SC::NT, SC::SMEM) != cudaSuccess ||

@@ -4,6 +4,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "per_device.h"
+
 #include <cstdint>
 
 namespace gmg {
@@ -92,7 +94,8 @@ struct AxisOp {
 
 // Device flag of the bounded device-side waits (TMA gathers, tensor-core
 // MMA completion): set to GMG_ERR_TIMEOUT by a kernel whose wait expired;
-// read and cleared by gmg_tc_status.
+// read and cleared by gmg_tc_status.  One flag per device: the address
+// returned is that of the current device's copy.
 int* device_wait_flag();
 
 // Host-side count of kernel launches made by this library (all launchers

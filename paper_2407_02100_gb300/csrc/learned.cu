@@ -669,6 +669,23 @@ int gmg_learned_train(gmg_problem* p, int n_samples, const int* sample_vertices,
   return cudaDeviceSynchronize() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
 }
 
+int gmg_exact_patch_solve(int dim, int degree, int n, const double* w, const double* r, double* d_exact,
+                          double* d_fd) {
+  if ((dim != 2 && dim != 3) || degree < 1 || degree > kMaxK || n < 0 || (n > 0 && (!w || !r || !d_exact || !d_fd)))
+    return GMG_ERR_INVALID_ARG;
+  if (n == 0) return GMG_OK;
+  const Shape sh = make_shape(dim, degree, kRank, kHidden);
+  if (exact_smem(sh) > 220 * 1024) return GMG_ERR_UNSUPPORTED;
+  CHECK(upload_learned_tables(degree));
+  DevBuf buf;
+  const std::vector<double> dinv_h = fd_diag(dim, degree);
+  double* dinv = buf.get<double>(sh.nint);
+  if (!dinv) return GMG_ERR_OOM;
+  if (cudaMemcpy(dinv, dinv_h.data(), sh.nint * 8, cudaMemcpyHostToDevice) != cudaSuccess) return GMG_ERR_CUDA;
+  CHECK(launch_exact(sh, n, w, r, dinv, d_exact, d_fd, nullptr, nullptr, nullptr));
+  return cudaDeviceSynchronize() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+}
+
 int gmg_learned_corrections(const gmg_problem* p, int level, float* out, long long count) {
   if (!p || level < 0 || level >= (int)p->levels.size() || !out) return GMG_ERR_INVALID_ARG;
   if ((int)p->corr.size() <= level || !p->corr[level]) return GMG_ERR_INVALID_ARG;

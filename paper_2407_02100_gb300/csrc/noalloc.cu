@@ -11,8 +11,17 @@
 // fast-diagonalisation diagonal 1/(lambda_x + lambda_y [+ lambda_z]) of the
 // patch.  Here it lives in a file-scope __device__ array sized for the
 // largest supported patch, (2*8-1)^3 doubles = 27 KB, which every GPU that
-// loads the library keeps until the process exits.  The coefficient tables go
-// to __constant__ memory with cudaMemcpyToSymbol, which allocates nothing.
+// loads the library keeps until the process exits.  Every call writes the
+// part of it that its degree uses with a small kernel on the caller's stream
+// (the eigenvalues travel as a kernel argument), then launches the colours.
+//
+// Set-up, once per device and degree, with that device current: the array's
+// device address is looked up (host code cannot use the symbol itself, which
+// names a host-side shadow) and the degree's coefficient tables are copied to
+// __constant__ memory with cudaMemcpyToSymbol, which allocates nothing but is
+// synchronous.  The generalised eigenproblem of the degree is solved on the
+// host once per process.  Later calls on that device and degree enqueue
+// kernels only.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -26,20 +35,61 @@
 namespace {
 
 constexpr int kNoAllocMaxDiag = 15 * 15 * 15;  // (2k-1)^3 for the largest degree k = 8
-constexpr int kMaxDevices = 64;
+constexpr int kMaxM = 15;                       // 2k-1 for k = 8
 
 __device__ __align__(256) double g_fd_diag[kNoAllocMaxDiag];
 
-std::mutex g_mutex;
-double* g_fd_diag_addr[kMaxDevices] = {};
+// 1D eigenvalues of the two-cell patch pencil K T = M T Lambda (App. A.3)
+struct Lambda1d {
+  double v[kMaxM];
+};
 
-// Device address of g_fd_diag on the current device.  Host code cannot use
-// the symbol itself (it names a host-side shadow), so the address is looked
-// up once per device with that device current, then cached.
-int scratch_address(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GMG_ERR_CUDA;
+// diag[t] = 1 / (lambda_x + lambda_y [+ lambda_z]) for the interior index t
+// of an m^dim patch (x fastest)
+__global__ void fill_fd_diag_kernel(double* __restrict__ diag, Lambda1d lam, int m, int dim, int nint) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nint; t += gridDim.x * blockDim.x) {
+    const int x = t % m, y = (t / m) % m, z = t / (m * m);
+    diag[t] = 1.0 / (lam.v[x] + lam.v[y] + (dim == 3 ? lam.v[z] : 0.0));
+  }
+}
+
+struct DegreeData {
+  bool ready = false;
+  Lambda1d lam{};
+  std::vector<double> Mc, Kc, Mp, Kp, Tp;
+};
+
+std::mutex g_mutex;
+DegreeData g_degree[gmg::kMaxDegree + 1];                  // host set-up math per degree
+double* g_fd_diag_addr[gmg::kMaxDevices] = {};             // array address per device
+bool g_tables_uploaded[gmg::kMaxDevices][gmg::kMaxDegree + 1] = {};
+
+// Host set-up of degree k (unit cells, level independent), solved once.
+int degree_data(int k, const DegreeData** out) {
+  DegreeData& d = g_degree[k];
+  if (!d.ready) {
+    const int m = 2 * k - 1, C = 2 * k + 1;
+    std::vector<double> Mi, Ki, lp;
+    gmg::cell_matrices_1d(k, d.Mc, d.Kc);
+    gmg::assembled_1d(k, 2, 1, m, 0, C, d.Mp, d.Kp);
+    gmg::assembled_1d(k, 2, 1, m, 1, m, Mi, Ki);
+    if (!gmg::generalized_eigen_mirror(m, Mi, Ki, d.Tp, lp) || (int)lp.size() != m) return GMG_ERR_INVALID_ARG;
+    for (int i = 0; i < m; ++i) d.lam.v[i] = lp[i];
+    d.ready = true;
+  }
+  *out = &d;
+  return GMG_OK;
+}
+
+// Per-device set-up for degree k on the current device: the array's address
+// and the degree's __constant__ tables.
+int device_setup(int k, double** diag, Lambda1d* lam) {
+  const int dev = gmg::current_device();
+  if (dev < 0) return GMG_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mutex);
+  const DegreeData* d = nullptr;
+  int st = degree_data(k, &d);
+  if (st != GMG_OK) return st;
   if (!g_fd_diag_addr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_fd_diag) != cudaSuccess || !p) {
@@ -48,7 +98,14 @@ int scratch_address(double** out) {
     }
     g_fd_diag_addr[dev] = static_cast<double*>(p);
   }
-  *out = g_fd_diag_addr[dev];
+  if (!g_tables_uploaded[dev][k]) {
+    st = gmg::upload_patch_tables<double>(k, d->Mp.data(), d->Kp.data(), d->Tp.data(), d->Mc.data(),
+                                          d->Kc.data(), nullptr);
+    if (st != GMG_OK) return st;
+    g_tables_uploaded[dev][k] = true;
+  }
+  *diag = g_fd_diag_addr[dev];
+  *lam = d->lam;
   return GMG_OK;
 }
 
@@ -62,32 +119,20 @@ extern "C" int gmg_smooth_noalloc(int dim, int degree, int n_cells, double dampi
   if ((long long)n_cells * degree + 1 > (1 << 20)) return GMG_ERR_INVALID_ARG;
   if (!std::isfinite(damping) || n_sweeps < 0 || !u || !b || (const double*)u == b)
     return GMG_ERR_INVALID_ARG;
-  const int k = degree, m = 2 * k - 1, C = 2 * k + 1;
+  const int k = degree, m = 2 * k - 1;
   const long long nint = dim == 3 ? (long long)m * m * m : (long long)m * m;
-  if (nint > kNoAllocMaxDiag) return GMG_ERR_INVALID_ARG;
+  if (nint > kNoAllocMaxDiag || m > kMaxM) return GMG_ERR_INVALID_ARG;
 
   double* diag = nullptr;
-  int st = scratch_address(&diag);
+  Lambda1d lam;
+  int st = device_setup(k, &diag, &lam);
   if (st != GMG_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-  // host set-up math (unit cells, level independent) and constant tables
-  std::vector<double> Mc, Kc, Mp, Kp, Mi, Ki, Tp, lp;
-  cell_matrices_1d(k, Mc, Kc);
-  assembled_1d(k, 2, 1, m, 0, C, Mp, Kp);
-  assembled_1d(k, 2, 1, m, 1, m, Mi, Ki);
-  if (!generalized_eigen_mirror(m, Mi, Ki, Tp, lp)) return GMG_ERR_INVALID_ARG;
-  st = upload_patch_tables<double>(k, Mp.data(), Kp.data(), Tp.data(), Mc.data(), Kc.data(), s);
-  if (st != GMG_OK) return st;
-  std::vector<double> dinv(nint);
-  for (long long t = 0; t < nint; ++t) {
-    int x = (int)(t % m), y = (int)((t / m) % m), z = (int)(t / ((long long)m * m));
-    dinv[t] = 1.0 / (lp[x] + lp[y] + (dim == 3 ? lp[z] : 0.0));
-  }
-  // the whole used part of the shared array is rewritten by every call
-  if (cudaMemcpyAsync(diag, dinv.data(), nint * sizeof(double), cudaMemcpyHostToDevice, s) !=
-      cudaSuccess)
-    return GMG_ERR_CUDA;
+  // the part of the shared array this degree uses is rewritten on every call
+  fill_fd_diag_kernel<<<(int)((nint + 255) / 256), 256, 0, s>>>(diag, lam, m, dim, (int)nint);
+  count_launch();
+  if (cudaGetLastError() != cudaSuccess) return GMG_ERR_CUDA;
 
   PatchLaunch pl;
   pl.g.dim = dim;

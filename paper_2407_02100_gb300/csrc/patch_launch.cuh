@@ -51,14 +51,14 @@ struct ApplyCfg {
 };
 
 static int sm_count() {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-      sms = 152;
+  static PerDevice<int> sms_dev;
+  int* const sms = sms_dev.get();
+  if (!sms) return 152;
+  if (*sms == 0) {
+    if (cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, current_device()) != cudaSuccess || *sms <= 0)
+      *sms = 152;
   }
-  return sms;
+  return *sms;
 }
 
 template <typename KernelT>
@@ -98,7 +98,10 @@ static int launch_table_cfg(PatchTable& tab, const T* dinv, cudaStream_t s) {
   constexpr int SMEM = PPC * Z::per_patch(NBUF) * (int)sizeof(T) + (ME > 0 ? 128 : 0);
   static_assert(SMEM <= 227 * 1024, "sweep kernel shared memory exceeds the per-CTA limit");
   auto kern = patch_colour_kernel<DIM, K, NT, PPC, NBUF, ME>;
-  static int per_sm = 0;  // resident CTAs per SM (persistent grid)
+  static PerDevice<int> per_sm_dev;  // resident CTAs per SM (persistent grid)
+  int* const per_sm_p = per_sm_dev.get();
+  if (!per_sm_p) return GMG_ERR_CUDA;
+  int& per_sm = *per_sm_p;
   if (per_sm == 0) {
     if (prepare(kern, SMEM) != GMG_OK) return GMG_ERR_CUDA;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, SMEM) != cudaSuccess ||
@@ -198,10 +201,12 @@ template <int DIM, int K, int BX, int BY, int BZ, int NT>
 static int apply_cfg(const ApplyLaunch& al, const T* x, T* y, const T* bvec, cudaStream_t s) {
   using D = ApplyDims<DIM, K, BX, BY, BZ>;
   auto kern = apply_kernel<DIM, K, BX, BY, BZ, NT>;
-  static bool ready = false;  // attribute set once (also keeps graph capture free of it)
-  if (!ready) {
+  static PerDevice<bool> ready_dev;  // attribute set once per device (also keeps graph capture free of it)
+  bool* const ready = ready_dev.get();
+  if (!ready) return GMG_ERR_CUDA;
+  if (!*ready) {
     if (prepare(kern, D::SMEM_BYTES) != GMG_OK) return GMG_ERR_CUDA;
-    ready = true;
+    *ready = true;
   }
   const long long n = al.g.n;
   const long long ntile = ((n + BX - 1) / BX) * ((n + BY - 1) / BY) * (DIM == 3 ? (n + BZ - 1) / BZ : 1);

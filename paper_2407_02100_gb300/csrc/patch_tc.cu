@@ -534,7 +534,10 @@ template <int K, bool SPLIT>
 int launch_k(PatchTable& tab, const float* dinv, cudaStream_t s) {
   using D = TcDims<K, SPLIT>;
   auto kern = patch_tc_kernel<K, SPLIT>;
-  static int per_sm = 0;
+  static PerDevice<int> per_sm_dev;
+  int* const per_sm_p = per_sm_dev.get();
+  if (!per_sm_p) return GMG_ERR_CUDA;
+  int& per_sm = *per_sm_p;
   if (per_sm == 0) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, D::SMEM) != cudaSuccess)
       return GMG_ERR_CUDA;
@@ -558,11 +561,13 @@ int launch_k(PatchTable& tab, const float* dinv, cudaStream_t s) {
   }
   tab.total_groups = g;
   if (g <= 0) return GMG_OK;
-  static int sms = 0;
+  static PerDevice<int> sms_dev;
+  int* const sms_p = sms_dev.get();
+  if (!sms_p) return GMG_ERR_CUDA;
+  int& sms = *sms_p;
   if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, current_device()) != cudaSuccess || sms <= 0)
+      sms = 152;
   }
   void* bops = nullptr;
   void* errp = nullptr;
@@ -607,12 +612,17 @@ void fill(PatchEntry& e, const PatchLaunch& pl, void* u, const void* b) {
 }  // namespace tc
 
 int* device_wait_flag() {
-  static int* flag = nullptr;
-  if (!flag) {
+  static PerDevice<int*> flag_dev;
+  int** const flag = flag_dev.get();
+  if (!flag) return nullptr;
+  if (!*flag) {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, tc::g_tc_error) == cudaSuccess) flag = static_cast<int*>(p);
+    if (cudaGetSymbolAddress(&p, tc::g_tc_error) == cudaSuccess)
+      *flag = static_cast<int*>(p);
+    else
+      cudaGetLastError();
   }
-  return flag;
+  return *flag;
 }
 
 bool tc_supported(int dim, int k) { return dim == 3 && k >= tc::kMinK && k <= tc::kMaxK; }

@@ -114,6 +114,18 @@ struct gmg_problem {
   cudaGraphExec_t cg_exec = nullptr;
   const void* cg_graph_u = nullptr;
   long long cg_graph_kernels = 0;
+  // per-phase timing of the CG (gmg_set_phase_timing): event pairs recorded
+  // on the stream around each outermost phase, summed into phase_ms at the
+  // solver's synchronisation points; events are pooled and reused
+  bool phase_timing = false;
+  int phase_depth = 0;
+  struct PhaseMark {
+    int phase;
+    cudaEvent_t start, stop;
+  };
+  std::vector<PhaseMark> phase_marks;
+  std::vector<cudaEvent_t> event_pool;
+  double phase_ms[GMG_PHASE_COUNT] = {};
 };
 
 namespace gmg {
@@ -124,6 +136,24 @@ namespace detail {
     int st_ = (x);                 \
     if (st_ != GMG_OK) return st_; \
   } while (0)
+
+// Times the enclosed launches as one phase when phase timing is on and no
+// enclosing scope is open (the outermost phase owns the time of nested ones).
+class PhaseScope {
+ public:
+  PhaseScope(gmg_problem* p, int phase);
+  ~PhaseScope();
+  PhaseScope(const PhaseScope&) = delete;
+  PhaseScope& operator=(const PhaseScope&) = delete;
+
+ private:
+  gmg_problem* p_;
+  int phase_;
+  cudaEvent_t start_ = nullptr;
+};
+// add the elapsed times of the recorded phases (stream already synchronised)
+void collect_phases(gmg_problem* p);
+void release_phase_events(gmg_problem* p);
 
 int dalloc(gmg_problem* p, void** ptr, size_t bytes);
 // forget the captured outer-CG iteration (anything the V-cycle launches changed)

@@ -34,7 +34,10 @@ static int apply_var_impl(const LevelGeom& g, long long n_elems, const T* x, T* 
 // persistent grid of the variable-coefficient sweep kernel (resident CTAs per SM)
 template <int DIM, int K, bool TMA>
 static int var_grid(int n_patches) {
-  static int per_sm = 0;
+  static PerDevice<int> per_sm_dev;  // resident CTAs on the whole device
+  int* const per_sm_p = per_sm_dev.get();
+  if (!per_sm_p) return -1;
+  int& per_sm = *per_sm_p;
   if (per_sm == 0) {
     int dev = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, patch_var_kernel<DIM, K, kVarThreads, TMA>,

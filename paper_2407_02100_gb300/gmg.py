@@ -35,7 +35,9 @@ EXPORTS = ["gmg_create", "gmg_destroy", "gmg_vector_layout", "gmg_level_info",
            "gmg_set_coefficient", "gmg_set_local_solver", "gmg_learned_train",
            "gmg_learned_corrections", "gmg_mlp_loss_grad", "gmg_tc_status", "gmg_tc_probe",
            "gmg_set_slab_width", "gmg_slab_width", "gmg_set_shared_faces", "gmg_shared_faces",
-           "gmg_set_three_pass_operator", "gmg_three_pass_operator"]
+           "gmg_set_three_pass_operator", "gmg_three_pass_operator", "gmg_exact_patch_solve",
+           "gmg_set_phase_timing", "gmg_fma_peak"]
+PHASES = ("smooth", "operator", "transfer", "coarse", "vector")
 GMG_LOCAL_FD_MEAN, GMG_LOCAL_LEARNED = 0, 1
 GMG_SWEEP_COMBINED, GMG_SWEEP_SEPARATED, GMG_SWEEP_BATCHED = 0, 1, 2
 
@@ -49,7 +51,8 @@ class GmgDesc(ctypes.Structure):
 class GmgSolveStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
                 ("initial_residual", ctypes.c_double), ("final_residual", ctypes.c_double),
-                ("relative_residual", ctypes.c_double), ("residual_history", ctypes.c_double * 64)]
+                ("relative_residual", ctypes.c_double), ("residual_history", ctypes.c_double * 64),
+                ("phase_ms", ctypes.c_double * 5)]
 
 
 class GmgError(RuntimeError):
@@ -103,6 +106,9 @@ def lib():
                                   ctypes.POINTER(d), ctypes.POINTER(i)],
             "gmg_learned_corrections": [vp, i, vp, ll],
             "gmg_mlp_loss_grad": [i, i, i, i, i, vp, vp, vp, vp, vp, ctypes.POINTER(d), vp],
+            "gmg_exact_patch_solve": [i, i, i, vp, vp, vp, vp],
+            "gmg_set_phase_timing": [vp, i],
+            "gmg_fma_peak": [i, ctypes.POINTER(d)],
             "gmg_smooth_noalloc": [i, i, i, d, vp, vp, i, i, vp],
             "gmg_status_string": [i],
             "gmg_tc_status": [],
@@ -209,6 +215,22 @@ def cg_gmg_solve(h, u, b, rtol=1e-10, max_it=100, raise_on_error=True):
     return status, st
 
 
+def gmg_fma_peak(precision):
+    """Measured FMA peak of the current device in TFLOP/s (GMG_FP64 or GMG_FP32)."""
+    out = ctypes.c_double()
+    _check("gmg_fma_peak", lib().gmg_fma_peak(precision, ctypes.byref(out)))
+    return out.value
+
+
+def gmg_set_phase_timing(h, enable):
+    _check("gmg_set_phase_timing", lib().gmg_set_phase_timing(h, 1 if enable else 0))
+
+
+def phase_times(stats):
+    """{phase name: GPU milliseconds} from a gmg_solve_stats."""
+    return {name: stats.phase_ms[i] for i, name in enumerate(PHASES)}
+
+
 def gmg_patch_fd_1d(degree):
     """Host-only: (M, K, T, lambda) of the two-unit-cell patch (numpy)."""
     m = 2 * degree - 1
@@ -279,6 +301,17 @@ def gmg_mlp_loss_grad(dim, degree, rank, hidden, params, X, R, DFD, DEX):
         dim, degree, rank, hidden, X.shape[0], _ptr(params), _ptr(X), _ptr(R), _ptr(DFD), _ptr(DEX),
         ctypes.byref(loss), _ptr(grads)))
     return loss.value, grads
+
+
+def gmg_exact_patch_solve(dim, degree, w, r):
+    """w: CUDA float64 [n, 2^dim] cell weights (geometric mean 1 per row), r:
+    CUDA float64 [n, m^dim] residuals.  Returns (d_exact, d_fd) tensors."""
+    import torch
+    d_ex = torch.zeros_like(r)
+    d_fd = torch.zeros_like(r)
+    _check("gmg_exact_patch_solve", lib().gmg_exact_patch_solve(
+        dim, degree, r.shape[0], _ptr(w), _ptr(r), _ptr(d_ex), _ptr(d_fd)))
+    return d_ex, d_fd
 
 
 def gmg_kernel_launch_count():

@@ -15,6 +15,7 @@ from oracle.mesh import Mesh
 from oracle.smoother import PatchSmoother
 from paper_2407_02100_gb300 import inputs
 
+FP32_RTOL = 1e-5
 pytestmark = pytest.mark.gpu
 
 
@@ -138,10 +139,12 @@ def test_pcg_iterations_and_solution(gmg, k, n):
     assert rel(sols[0], sols[1]) <= 1e-11
 
 
-@pytest.mark.parametrize("k,n", [(7, 3), (8, 2), (7, 2)])
+@pytest.mark.parametrize("k,n", [(7, 3), (8, 2), (7, 2), (7, 4)])
 def test_fp32_each_colour_matches_oracle(gmg, k, n):
     """FP32 data (the oracle takes the FP32-rounded inputs): each colour step
-    of the form is as close to the oracle as the closure kernel's."""
+    of the shared-face form (the FP32 default from k = 7) and of the closure
+    form is within the FP32 sweep tolerance 1e-5 of the oracle (relative
+    2-norm over all nodes, as for every FP32 sweep)."""
     m = Mesh(3, k, n)
     s = PatchSmoother(m)
     P = gmg.Problem(3, k, n, n_levels=1, precision=gmg.GMG_FP32)
@@ -158,7 +161,7 @@ def test_fp32_each_colour_matches_oracle(gmg, k, n):
             gmg.gmg_smooth_colour(P.h, 0, ud, bd, c)
             err.append(rel(P.from_device(ud), ref))
         gmg.gmg_set_shared_faces(P.h, True)
-        assert err[0] <= 2 * err[1] + 1e-6 and err[0] <= 1e-4, (c, err)
+        assert max(err) <= FP32_RTOL, (c, err)
 
 
 @pytest.mark.parametrize("k,n,omega", [(7, 3, 1.0), (7, 2, 0.8), (8, 2, 1.0)])

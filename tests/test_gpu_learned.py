@@ -119,3 +119,43 @@ def test_sample_ids_span_all_levels(gmg):
     res = torch.tensor(np.random.default_rng(42).standard_normal((9, nint)), device="cuda")
     hist, kept = gmg.gmg_learned_train(P.h, np.arange(total - 9, total), res, steps=5, batch=9)
     assert len(hist) == 5 and all(np.isfinite(hist))
+
+
+@pytest.mark.parametrize("dim,k,n", [(3, 2, 8), (3, 3, 8), (2, 3, 16), (3, 1, 8)])
+def test_exact_patch_targets_match_oracle(gmg, dim, k, n):
+    """The training targets (the CUDA exact dense patch solve and the damped
+    FD solve that gmg_learned_train generates) against the oracle's
+    VarPatchSmoother local solves, on sampled patches of every level of a
+    variable-coefficient hierarchy (geometric-mean coarsening), element-wise.
+    The oracle solves A_j d = r at the level's h; the kernel works in
+    reference units, Ahat(w) = A_j / (h^{d-2} abar), so its outputs are
+    compared with h^{d-2} abar times the oracle's."""
+    import torch
+    from oracle.varcoef import VarMultigrid, patch_cell_coefs
+    coef = inputs.lognormal_coefficient(dim, n, 51, sigma=1.0, corr_len=0.15)
+    mg_ex = VarMultigrid(dim, k, n, 3, coef, "exact")
+    rng = np.random.default_rng(52)
+    for lvl, (m, cf) in enumerate(zip(mg_ex.meshes, mg_ex.coefs)):
+        V = m.vertices()
+        if len(V) == 0:
+            continue
+        V = V[rng.choice(len(V), size=min(len(V), 24), replace=False)]
+        ex = mg_ex.smoothers[lvl]
+        fd = VarPatchSmoother(m, cf, "fd_mean")
+        nint = (2 * k - 1) ** dim
+        W, R, want_ex, want_fd = [], [], [], []
+        for v in V:
+            cc = patch_cell_coefs(m, cf, v)
+            abar = np.exp(np.mean(np.log(cc)))
+            r = rng.standard_normal(nint)
+            scale = m.h ** (dim - 2) * abar
+            W.append(cc / abar)
+            R.append(r)
+            want_ex.append(scale * ex.local_solve(v, r))
+            want_fd.append(scale * fd.local_solve(v, r))
+        cuda = lambda a: torch.tensor(np.array(a), dtype=torch.float64, device="cuda")
+        d_ex, d_fd = gmg.gmg_exact_patch_solve(dim, k, cuda(W), cuda(R))
+        d_ex, d_fd = d_ex.cpu().numpy(), d_fd.cpu().numpy()
+        for got, want in ((d_ex, np.array(want_ex)), (d_fd, np.array(want_fd))):
+            err = np.linalg.norm(got - want, axis=1) / np.linalg.norm(want, axis=1)
+            assert err.max() <= 1e-12, (lvl, err.max())
