@@ -338,12 +338,27 @@ int gmg_set_local_solver(gmg_problem* p, int solver);
  * evaluates the network (FP16-rounded weights, FP32 accumulation) on every
  * patch of every level and keeps a patch's correction only if it lowers the
  * local energy-norm error on a probe residual (damped FD is the fallback).
- * loss_history (HOST, `steps` entries) and kept_patches may be NULL.  On
- * success the local solver becomes GMG_LOCAL_LEARNED.  Allocates the
- * per-patch corrections (m^d R + R floats per patch and level). */
+ * Finally a level judge decides per level whether the correction is used at
+ * all: the FP64 CG solves a fixed probe right-hand side to 1e-10 with no
+ * level corrected, then, from the coarsest level up, a level keeps its
+ * correction only if the iteration count drops below the best so far
+ * (see gmg_learned_levels).  loss_history (HOST, `steps` entries) and
+ * kept_patches (patches kept by the per-patch gate, all levels) may be NULL.
+ * On success the local solver becomes GMG_LOCAL_LEARNED.  Allocates the
+ * per-patch corrections (m^d R + R floats per patch and level) and
+ * temporaries; synchronises the device. */
 int gmg_learned_train(gmg_problem* p, int n_samples, const int* sample_vertices,
                       const double* residuals, int steps, int batch, double lr, unsigned seed,
                       double* loss_history, int* kept_patches);
+
+/* Levels whose learned correction the smoother applies under
+ * GMG_LOCAL_LEARNED, as a bit mask (bit l = level l, 0 = coarsest), chosen
+ * by the level judge of gmg_learned_train; the other levels use damped FD.
+ * gmg_learned_set_levels overrides the choice (every set bit must name a
+ * trained level).  Errors: INVALID_ARG (null or constant-coefficient
+ * problem, bits beyond the levels or on untrained levels). */
+int gmg_learned_levels(const gmg_problem* p);
+int gmg_learned_set_levels(gmg_problem* p, int mask);
 
 /* Copy the per-patch corrections of `level` (patches in lexicographic vertex
  * order, each U (m^d x R, row-major) then s (R)) to the HOST array out of

@@ -214,7 +214,8 @@ int smooth_colour(gmg_problem* p, int level, void* u, const void* b, int colour)
   const PatchLaunch pl = colour_launch(p->levels[level], colour, p->desc.damping);
   if (p->varcoef) {
     if (pl.n_patches == 0) return GMG_OK;
-    const float* corr = p->local_solver == GMG_LOCAL_LEARNED ? p->corr[level] : nullptr;
+    const float* corr =
+        p->local_solver == GMG_LOCAL_LEARNED && ((p->corr_levels >> level) & 1u) ? p->corr[level] : nullptr;
     if (p->esize == 8)
       return launch_patch_var<double>(pl, (double*)u, (const double*)b, (const double*)p->coef[level],
                                       (const double*)p->dinv, corr, p->corr_rank, p->stream);
@@ -913,6 +914,7 @@ int gmg_set_coefficient(gmg_problem* p, const double* coef) {
   for (int l = 0; l < L; ++l) CHECK(upload_table(p, &p->coef[l], lev[l]));
   p->coarse_n = (int)nint0;
   p->corr.assign(L, nullptr);
+  p->corr_levels = 0;
   p->varcoef = true;
   p->local_solver = GMG_LOCAL_FD_MEAN;
   return cudaDeviceSynchronize() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
@@ -926,8 +928,9 @@ int gmg_set_local_solver(gmg_problem* p, int solver) {
     return GMG_OK;
   }
   if (solver == GMG_LOCAL_LEARNED) {
-    for (float* c : p->corr)
-      if (!c) return GMG_ERR_INVALID_ARG;  // train first
+    bool trained = false;
+    for (float* c : p->corr) trained = trained || c;
+    if (!trained) return GMG_ERR_INVALID_ARG;  // train first
     p->local_solver = solver;
     return GMG_OK;
   }

@@ -475,6 +475,59 @@ void patch_features(const std::vector<double>& coef, int dim, int n, const std::
   }
 }
 
+// Level judge: plain FD is the fallback and the judge of the learned
+// correction at the level of the whole solver.  With the corrections of no
+// level in use, the FP64 CG (V-cycle preconditioner, the problem's own
+// settings) solves a fixed probe right-hand side to the benchmark tolerance;
+// then, level by level from the coarsest, a level's correction stays in use
+// only if it lowers the iteration count below the best so far.  Levels that
+// buy no iteration cost only time, so they fall back to damped FD.
+int judge_levels(gmg_problem* p) {
+  const int L = (int)p->levels.size();
+  const Level& F = p->levels[L - 1];
+  const LevelGeom& g = F.g;
+  std::vector<double> probe((size_t)F.n_elems, 0.0);
+  unsigned long long x = 0x9E3779B97F4A7C15ull;  // fixed xorshift sequence
+  for (int i2 = (g.dim == 3 ? 1 : 0); i2 < (g.dim == 3 ? g.N - 1 : 1); ++i2)
+    for (int i1 = 1; i1 < g.N - 1; ++i1)
+      for (int i0 = 1; i0 < g.N - 1; ++i0) {
+        x ^= x << 13;
+        x ^= x >> 7;
+        x ^= x << 17;
+        probe[(size_t)(i0 + (long long)g.py * i1 + g.pz * i2)] = (double)(x >> 11) * 0x1.0p-52 - 1.0;
+      }
+  DevBuf buf;
+  double* b = buf.get<double>(probe.size());
+  double* u = buf.get<double>(probe.size());
+  if (!b || !u) return GMG_ERR_OOM;
+  if (cudaMemcpy(b, probe.data(), probe.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) return GMG_ERR_CUDA;
+  auto iterations = [&](unsigned mask, int* its) -> int {
+    p->corr_levels = mask;
+    drop_cg_graph(p);
+    if (cudaMemsetAsync(u, 0, probe.size() * 8, p->stream) != cudaSuccess) return GMG_ERR_CUDA;
+    gmg_solve_stats st;
+    const int rc = cg_gmg_solve(p, u, b, 1e-10, 500, &st);
+    if (rc == GMG_ERR_CUDA || rc == GMG_ERR_INVALID_ARG) return rc;
+    *its = rc == GMG_OK ? st.iterations : 1 << 30;  // breakdown or no convergence: reject
+    return GMG_OK;
+  };
+  int best = 0;
+  CHECK(iterations(0u, &best));
+  unsigned mask = 0u;
+  for (int l = 0; l < L; ++l) {
+    if (!p->corr[l]) continue;
+    int its = 0;
+    CHECK(iterations(mask | (1u << l), &its));
+    if (its < best) {
+      best = its;
+      mask |= 1u << l;
+    }
+  }
+  p->corr_levels = mask;
+  drop_cg_graph(p);
+  return cudaDeviceSynchronize() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+}
+
 }  // namespace
 
 extern "C" {
@@ -666,7 +719,24 @@ int gmg_learned_train(gmg_problem* p, int n_samples, const int* sample_vertices,
   }
   if (kept_patches) *kept_patches = kept_total;
   p->local_solver = GMG_LOCAL_LEARNED;
-  return cudaDeviceSynchronize() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return GMG_ERR_CUDA;
+  return judge_levels(p);
+}
+
+int gmg_learned_levels(const gmg_problem* p) {
+  if (!p || !p->varcoef) return GMG_ERR_INVALID_ARG;
+  return (int)p->corr_levels;
+}
+
+int gmg_learned_set_levels(gmg_problem* p, int mask) {
+  if (!p || !p->varcoef || mask < 0) return GMG_ERR_INVALID_ARG;
+  const int L = (int)p->levels.size();
+  if (L < 31 && (mask >> L) != 0) return GMG_ERR_INVALID_ARG;
+  for (int l = 0; l < L; ++l)
+    if (((mask >> l) & 1) && ((int)p->corr.size() <= l || !p->corr[l])) return GMG_ERR_INVALID_ARG;
+  drop_cg_graph(p);
+  p->corr_levels = (unsigned)mask;
+  return GMG_OK;
 }
 
 int gmg_exact_patch_solve(int dim, int degree, int n, const double* w, const double* r, double* d_exact,

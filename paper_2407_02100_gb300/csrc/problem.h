@@ -88,6 +88,7 @@ struct gmg_problem {
   int local_solver = 0;             // GMG_LOCAL_FD_MEAN or GMG_LOCAL_LEARNED
   int corr_rank = 0;
   std::vector<float*> corr;         // per level: [patches][m^d * rank + rank] or null
+  unsigned corr_levels = 0;         // bit l: level l applies its correction (level judge)
   double* coarse_inv = nullptr;     // dense inverse of the coarsest interior matrix
   int coarse_n = 0;
   std::vector<void*> owned;

@@ -36,7 +36,7 @@ EXPORTS = ["gmg_create", "gmg_destroy", "gmg_vector_layout", "gmg_level_info",
            "gmg_learned_corrections", "gmg_mlp_loss_grad", "gmg_tc_status", "gmg_tc_probe",
            "gmg_set_slab_width", "gmg_slab_width", "gmg_set_shared_faces", "gmg_shared_faces",
            "gmg_set_three_pass_operator", "gmg_three_pass_operator", "gmg_exact_patch_solve",
-           "gmg_set_phase_timing", "gmg_fma_peak"]
+           "gmg_set_phase_timing", "gmg_fma_peak", "gmg_learned_levels", "gmg_learned_set_levels"]
 PHASES = ("smooth", "operator", "transfer", "coarse", "vector")
 GMG_LOCAL_FD_MEAN, GMG_LOCAL_LEARNED = 0, 1
 GMG_SWEEP_COMBINED, GMG_SWEEP_SEPARATED, GMG_SWEEP_BATCHED = 0, 1, 2
@@ -109,6 +109,8 @@ def lib():
             "gmg_exact_patch_solve": [i, i, i, vp, vp, vp, vp],
             "gmg_set_phase_timing": [vp, i],
             "gmg_fma_peak": [i, ctypes.POINTER(d)],
+            "gmg_learned_levels": [vp],
+            "gmg_learned_set_levels": [vp, i],
             "gmg_smooth_noalloc": [i, i, i, d, vp, vp, i, i, vp],
             "gmg_status_string": [i],
             "gmg_tc_status": [],
@@ -276,6 +278,18 @@ def gmg_learned_train(h, sample_vertices, residuals, steps=300, batch=1024, lr=3
         h, len(verts), verts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _ptr(residuals), steps, batch,
         lr, seed, hist, ctypes.byref(kept)))
     return list(hist)[:steps], kept.value
+
+
+def gmg_learned_levels(h):
+    """Bit mask of the levels whose learned correction is in use."""
+    mask = lib().gmg_learned_levels(h)
+    if mask < 0:
+        _check("gmg_learned_levels", mask)
+    return mask
+
+
+def gmg_learned_set_levels(h, mask):
+    _check("gmg_learned_set_levels", lib().gmg_learned_set_levels(h, int(mask)))
 
 
 def learned_patch_count(dim, n_cells, n_levels):

@@ -63,6 +63,7 @@ def test_training_reduces_loss_and_sweep_matches_oracle(gmg):
     assert hist[-1] < 0.8 * hist[0], (hist[0], hist[-1])
     npatch, nint, rank = (n - 1) ** dim, (2 * k - 1) ** dim, 4
     assert 0 < kept <= npatch
+    gmg.gmg_learned_set_levels(P.h, 1)     # apply the correction whatever the level judge chose
     C = gmg.gmg_learned_corrections(P.h, 0, npatch, nint * rank + rank).astype(np.float64)
     corr = {}
     for vid in range(npatch):
@@ -98,7 +99,39 @@ def test_learned_correction_gains_over_plain_fd(gmg):
         u = P.zeros(dtype=torch.float64)
         _, st = gmg.cg_gmg_solve(P.h, u, P.to_device(b, dtype=torch.float64), 1e-10, 200)
         its[mode] = st.iterations
+        if mode == "learned":
+            assert gmg.gmg_learned_levels(P.h) != 0     # the level judge kept some level
     assert its["learned"] < its["fd"], its
+
+
+def test_level_judge_falls_back_to_fd_where_the_correction_buys_nothing(gmg):
+    """3D Q2 16^3, three levels, a mild field: the level judge keeps a
+    level's correction only if the probe solve needs fewer iterations with
+    it.  So the learned solver never needs more iterations than damped FD on
+    the probe, and on another right-hand side it stays within one.  With
+    every level forced on, the same solve matches the mask's choice or
+    does worse."""
+    import torch
+    dim, k, n, L = 3, 2, 16, 3
+    coef = inputs.lognormal_coefficient(dim, n, 23, sigma=0.5, corr_len=0.2)
+    b = inputs.random_nodal(dim, k, n, 24)
+    P = gmg.Problem(dim, k, n, n_levels=L)
+    gmg.gmg_set_coefficient(P.h, coef)
+    bd = P.to_device(b, dtype=torch.float64)
+    u = P.zeros(dtype=torch.float64)
+    _, st_fd = gmg.cg_gmg_solve(P.h, u, bd, 1e-10, 200)
+    _train(gmg, P, dim, k, n, steps=100)
+    mask = gmg.gmg_learned_levels(P.h)
+    assert 0 <= mask < 2 ** L
+    u.zero_()
+    _, st = gmg.cg_gmg_solve(P.h, u, bd, 1e-10, 200)
+    assert st.converged and st.iterations <= st_fd.iterations + 1, (st.iterations, st_fd.iterations, mask)
+    if mask == 0:   # no level kept: exactly the damped-FD solver
+        assert st.iterations == st_fd.iterations
+    gmg.gmg_learned_set_levels(P.h, 2 ** L - 1)
+    assert gmg.gmg_learned_levels(P.h) == 2 ** L - 1
+    with pytest.raises(gmg.GmgError):
+        gmg.gmg_learned_set_levels(P.h, 2 ** L)
 
 
 def test_sample_ids_span_all_levels(gmg):
