@@ -615,7 +615,8 @@ def c5_leg(gmg, inputs, torch, local):
                                                    seed=c["seed"])
                 torch.cuda.synchronize()
                 rec.update({"train_s": time.perf_counter() - t0, "loss_first": hist[0], "loss_last": hist[-1],
-                            "kept_patches": kept})
+                            "kept_patches": kept, "levels_kept_mask": gmg.gmg_learned_levels(P.h),
+                            "levels": P.n_levels})
                 del res
             b = P.to_device(rhs, dtype=torch.float64)
             u = P.zeros(dtype=torch.float64)
