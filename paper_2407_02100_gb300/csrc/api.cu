@@ -679,6 +679,17 @@ int gmg::detail::create_problem(const gmg_desc* d, gmg_problem* p, const CreateO
     double s = lp[x] + lp[y] + (dim == 3 ? lp[z] : 0.0);
     dinv[t] = 1.0 / s;
   }
+  if (p->esize == 8) {
+    // FP64 problems: the table is followed by its double-float split, the
+    // float pair (hi, lo) with hi + lo = 1 / (sum of eigenvalues) to about
+    // 48 bits, read by the shared-face sweep's double-float FD transforms
+    dinv.resize(2 * (size_t)nint);
+    for (int t = 0; t < nint; ++t) {
+      const float hi = (float)dinv[t], lo = (float)(dinv[t] - (double)hi);
+      float pair[2] = {hi, lo};
+      std::memcpy(&dinv[nint + t], pair, sizeof(pair));
+    }
+  }
   CHECK(upload_table(p, &p->dinv, dinv));
   // face buffer of the shared-face sweep: the largest colour of the finest
   // level; without memory for it the closure form is used.  FP64 problems

@@ -277,10 +277,15 @@ __global__ void __launch_bounds__(NT) patch_face_kernel(const __grid_constant__ 
                                                         const __grid_constant__ CUtensorMap bmap) {
   using Z = FaceSweepSmem<K>;
   constexpr int C = Z::C, M = Z::M, XB = Z::XB, FS = Z::FS, LINES = M * M;
+  // FP64: the FD transforms run in double-float arithmetic (pairs of floats
+  // in WB; the diagonal's float pairs follow the FP64 diagonal in dinv)
+  constexpr bool DF = sizeof(T) == 8;
   static_assert(PPC <= 32, "one lane of warp 0 issues the copies of one patch");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* const IN0 = reinterpret_cast<T*>(smem_raw + ((128 - (async::smem_u32(smem_raw) & 127)) & 127));
   T* const WB = IN0 + NBUF * PPC * Z::IN;
+  float2* const WB2 = reinterpret_cast<float2*>(WB);  // used when DF: same element size
+  const float2* const dinv_df = reinterpret_cast<const float2*>(fa.dinv + M * M * M);
   T* const SUMS = WB + PPC * Z::WB;
   __shared__ long long s_origin[2][PPC];
   __shared__ int s_x[2][PPC][3];     // closure origin (lattice coordinates)
@@ -406,36 +411,60 @@ __global__ void __launch_bounds__(NT) patch_face_kernel(const __grid_constant__ 
         acc = fma(-my, FY[i], fma(-ky, FY[M * M + i], acc));
         r[i] = fma(-mz, FZ[i], fma(-kz, FZ[M * M + i], acc));
       }
-      fd_forward<K>(r, y);
-      T* R = WB + q * Z::WB + M * ln;
+      if constexpr (DF) {
+        dfv rd[M], yd[M];
 #pragma unroll
-      for (int i = 0; i < M; ++i) R[i] = y[i];
+        for (int i = 0; i < M; ++i) rd[i] = df_from_double(r[i]);
+        fd_forward_df<K>(rd, yd);
+        float2* R = WB2 + q * Z::WB + M * ln;
+#pragma unroll
+        for (int i = 0; i < M; ++i) R[i] = make_float2(yd[i].hi, yd[i].lo);
+      } else {
+        fd_forward<K>(r, y);
+        T* R = WB + q * Z::WB + M * ln;
+#pragma unroll
+        for (int i = 0; i < M; ++i) R[i] = y[i];
+      }
     }
     __syncthreads();
     // ---- local solve by fast diagonalisation (App. A.3), in place in WB ----
     for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // forward y
       const int q = idx / LINES, l = idx % LINES;
-      fd_smem_line<K, true>(WB + q * Z::WB + (l % M) + (l / M) * M * M, M);
+      if constexpr (DF) fd_smem_line_df<K, true>(WB2 + q * Z::WB + (l % M) + (l / M) * M * M, M);
+      else fd_smem_line<K, true>(WB + q * Z::WB + (l % M) + (l / M) * M * M, M);
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // forward z, diagonal, backward z
       const int q = idx / LINES, l = idx % LINES;
-      fd_smem_line_solve<K>(WB + q * Z::WB + l, M * M, fa.dinv + l, M * M);
+      if constexpr (DF) fd_smem_line_solve_df<K>(WB2 + q * Z::WB + l, M * M, dinv_df + l, M * M);
+      else fd_smem_line_solve<K>(WB + q * Z::WB + l, M * M, fa.dinv + l, M * M);
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // backward y
       const int q = idx / LINES, l = idx % LINES;
-      fd_smem_line<K, false>(WB + q * Z::WB + (l % M) + (l / M) * M * M, M);
+      if constexpr (DF) fd_smem_line_df<K, false>(WB2 + q * Z::WB + (l % M) + (l / M) * M * M, M);
+      else fd_smem_line<K, false>(WB + q * Z::WB + (l % M) + (l / M) * M * M, M);
     }
     __syncthreads();
     // ---- backward FD along x and scatter (eq. "scatter") ----
     for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {
       const int q = idx / LINES, l = idx % LINES;
-      const T* R = WB + q * Z::WB + M * l;
-      T yv[M], d[M];
+      T d[M];
+      if constexpr (DF) {
+        const float2* R = WB2 + q * Z::WB + M * l;
+        dfv yv[M], dd[M];
 #pragma unroll
-      for (int i = 0; i < M; ++i) yv[i] = R[i];
-      fd_backward<K>(yv, d);
+        for (int i = 0; i < M; ++i) yv[i] = {R[i].x, R[i].y};
+        fd_backward_df<K>(yv, dd);
+#pragma unroll
+        for (int i = 0; i < M; ++i) d[i] = df_to_double(dd[i]);
+      } else {
+        const T* R = WB + q * Z::WB + M * l;
+        T yv[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) yv[i] = R[i];
+        fd_backward<K>(yv, d);
+      }
       T* __restrict__ row = fa.u + s_origin[cur][q] + 1 + fa.py * (l % M + 1) + fa.pz * (l / M + 1);
       if (om == T(1)) {
 #pragma unroll

