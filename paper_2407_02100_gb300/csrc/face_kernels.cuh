@@ -226,6 +226,139 @@ __global__ void __launch_bounds__(NT) face_kernel(const T* __restrict__ u, T* __
   }
 }
 
+// The face kernel of FP64 problems in double-float arithmetic: the node
+// values are read as doubles and split into float pairs, both stages
+// accumulate in Dot2 form with the float-pair patch matrices, and the face
+// fields are stored as float pairs (the same 8 bytes per entry as a double).
+template <int K, int NT>
+__global__ void __launch_bounds__(NT) face_kernel_df(const double* __restrict__ u, float2* __restrict__ faces,
+                                                     const __grid_constant__ FaceGeom fg, int bx, int by) {
+  using F = FaceCfg<K, NT>;
+  constexpr int C = F::C, M = F::M, FS = face_fields(K);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float2* const S = reinterpret_cast<float2*>(smem_raw);
+  int fam, blk;
+  if ((int)blockIdx.x < bx) { fam = 0; blk = blockIdx.x; }
+  else if ((int)blockIdx.x < bx + by) { fam = 1; blk = blockIdx.x - bx; }
+  else { fam = 2; blk = blockIdx.x - bx - by; }
+  const int per = fam == 0 ? F::FX : F::FYZ;
+  const long long f0 = (long long)blk * per;
+  const int nq = (int)min((long long)per, fg.nf[fam] - f0);
+  float2* const out = faces + fg.foff[fam] + f0 * FS;
+  auto ld = [](const float2 v) -> dfv { return {v.x, v.y}; };
+  auto st = [](const dfv v) -> float2 { return make_float2(v.hi, v.lo); };
+  if (fam == 0) {
+    float2* V = S;
+    float2* P = S + F::FX * C * C;
+    float2* Q = P + F::FX * C * M;
+    for (int t = threadIdx.x; t < nq * C * C; t += NT) {
+      const int q = t % nq, e = t / nq, y = e % C, z = e / C;
+      V[q * C * C + y * C + z] = st(df_from_double(u[face_origin<K>(fg, 0, f0 + q) + fg.py * y + fg.pz * z]));
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nq * C; t += NT) {
+      const int q = t / C, y = t % C;
+      dfv v[C];
+#pragma unroll
+      for (int z = 0; z < C; ++z) v[z] = ld(V[q * C * C + y * C + z]);
+#pragma unroll
+      for (int l = 0; l < M; ++l) {
+        df_acc a = {0.f, 0.f}, b = {0.f, 0.f};
+        patch_row_df<K, 0>(l, v, a);
+        patch_row_df<K, 1>(l, v, b);
+        P[(q * C + y) * M + l] = st(df_acc_value(a));
+        Q[(q * C + y) * M + l] = st(df_acc_value(b));
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nq * M; t += NT) {
+      const int q = t / M, l = t % M;
+      dfv p[C], r[C];
+#pragma unroll
+      for (int y = 0; y < C; ++y) {
+        p[y] = ld(P[(q * C + y) * M + l]);
+        r[y] = ld(Q[(q * C + y) * M + l]);
+      }
+      float2* o = out + (long long)q * FS + l * M;
+#pragma unroll
+      for (int j = 0; j < M; ++j) {
+        df_acc a = {0.f, 0.f}, b = {0.f, 0.f};
+        patch_row_df<K, 0>(j, p, a);
+        patch_row_df<K, 1>(j, p, b);
+        patch_row_df<K, 0>(j, r, b);
+        o[j] = st(df_acc_value(a));
+        o[M * M + j] = st(df_acc_value(b));
+      }
+    }
+    return;
+  }
+  float2* P = S + F::FYZ * (fam == 1 ? M * C : M * M);
+  float2* Q = P + F::FYZ * M * M;
+  if (fam == 1) {
+    float2* W = S;
+    for (int t = threadIdx.x; t < nq * M * C; t += NT) {
+      const int a = t % M, e = t / M, z = e % C, q = e / C;
+      W[(q * M + a) * C + z] = st(df_from_double(u[face_origin<K>(fg, 1, f0 + q) + a + fg.pz * z]));
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nq * M; t += NT) {
+      const int q = t / M, a = t % M;
+      dfv v[C];
+#pragma unroll
+      for (int z = 0; z < C; ++z) v[z] = ld(W[(q * M + a) * C + z]);
+#pragma unroll
+      for (int l = 0; l < M; ++l) {
+        df_acc x = {0.f, 0.f}, y = {0.f, 0.f};
+        patch_row_df<K, 0>(l, v, x);
+        patch_row_df<K, 1>(l, v, y);
+        P[(q * M + a) * M + l] = st(df_acc_value(x));
+        Q[(q * M + a) * M + l] = st(df_acc_value(y));
+      }
+    }
+  } else {
+    float2* Sz = S;
+    for (int t = threadIdx.x; t < nq * M * M; t += NT) {
+      const int a = t % M, e = t / M, b = e % M, q = e / M;
+      Sz[(q * M + a) * M + b] = st(df_from_double(u[face_origin<K>(fg, 2, f0 + q) + a + fg.py * b]));
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nq * M; t += NT) {
+      const int q = t / M, a = t % M;
+      dfv v[M];
+#pragma unroll
+      for (int b = 0; b < M; ++b) v[b] = ld(Sz[(q * M + a) * M + b]);
+#pragma unroll
+      for (int j = 0; j < M; ++j) {
+        df_acc x = {0.f, 0.f}, y = {0.f, 0.f};
+        patch_row_int_df<K, 0>(j, v, x);
+        patch_row_int_df<K, 1>(j, v, y);
+        P[(q * M + a) * M + j] = st(df_acc_value(x));
+        Q[(q * M + a) * M + j] = st(df_acc_value(y));
+      }
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nq * M; t += NT) {
+    const int q = t / M, l = t % M;
+    dfv p[M], r[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      p[a] = ld(P[(q * M + a) * M + l]);
+      r[a] = ld(Q[(q * M + a) * M + l]);
+    }
+    float2* o = out + (long long)q * FS + l * M;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      df_acc x = {0.f, 0.f}, y = {0.f, 0.f};
+      patch_row_int_df<K, 1>(i, p, x);
+      patch_row_int_df<K, 0>(i, r, x);
+      patch_row_int_df<K, 0>(i, p, y);
+      o[i] = st(df_acc_value(x));
+      o[M * M + i] = st(df_acc_value(y));
+    }
+  }
+}
+
 // Shared-memory plan of the shared-face sweep, per patch (elements of T):
 //   IN (NBUF copies): interior rows of b (TMA box rows of XB, as in the
 //       closure kernel), then the face blocks X0 X1 Y0 Y1 Z0 Z1 of the patch
@@ -379,7 +512,13 @@ __global__ void __launch_bounds__(NT) patch_face_kernel(const __grid_constant__ 
     for (int idx = threadIdx.x; idx < nvalid * Z::SUMS; idx += NT) {
       const int q = idx / Z::SUMS, e = idx % Z::SUMS;
       const T* F = IN + q * Z::IN + Z::NBIN + (e < FS ? 2 * FS : 4 * FS) + e % FS;
-      SUMS[idx] = F[0] + F[FS];
+      if constexpr (DF) {
+        const float2* F2 = reinterpret_cast<const float2*>(F);
+        const dfv v = df_add({F2[0].x, F2[0].y}, {F2[FS].x, F2[FS].y});
+        reinterpret_cast<float2*>(SUMS)[idx] = make_float2(v.hi, v.lo);
+      } else {
+        SUMS[idx] = F[0] + F[FS];
+      }
     }
     __syncthreads();
 
@@ -394,6 +533,51 @@ __global__ void __launch_bounds__(NT) patch_face_kernel(const __grid_constant__ 
       // sum) and those of row l for the z faces (H1[j][.], H2[j][.])
       const T* FY = (j < K - 1 ? FX + 2 * FS : j > K - 1 ? FX + 3 * FS : SUMS + q * Z::SUMS) + l * M;
       const T* FZ = (l < K - 1 ? FX + 4 * FS : l > K - 1 ? FX + 5 * FS : SUMS + q * Z::SUMS + FS) + j * M;
+      if constexpr (DF) {
+        // the same residual in double-float: faces and sums are float pairs
+        auto ld = [](const T* p, int i) -> dfv {
+          const float2 v = reinterpret_cast<const float2*>(p)[i];
+          return {v.x, v.y};
+        };
+        const dfv f10 = ld(FX, l * M + j), f20 = ld(FX, M * M + l * M + j);
+        const dfv f11 = ld(FX, FS + l * M + j), f21 = ld(FX, FS + M * M + l * M + j);
+        const int cj = j < K ? 0 : C - 1, cl = l < K ? 0 : C - 1;
+        float myh, myl, kyh, kyl, mzh, mzl, kzh, kzl;
+        patch_entry_df<K, 0, true>(j, cj, myh, myl);
+        patch_entry_df<K, 1, true>(j, cj, kyh, kyl);
+        patch_entry_df<K, 0, true>(l, cl, mzh, mzl);
+        patch_entry_df<K, 1, true>(l, cl, kzh, kzl);
+        const float sbf = (float)fa.sb;  // h^{2-d} = n, exact in float
+        dfv rd[M], yd[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+          const dfv bb = df_mul(df_from_double(Bq[i]), {sbf, 0.f});
+          df_acc acc = {bb.hi, bb.lo};
+          float h, lo;
+          if (band_lo(i + 1, K) == 0) {
+            patch_entry_df<K, 1, true>(i, 0, h, lo);
+            df_acc_add(acc, h, lo, f10);
+            patch_entry_df<K, 0, true>(i, 0, h, lo);
+            df_acc_add(acc, h, lo, f20);
+          }
+          if (band_hi(i + 1, K) == 2 * K) {
+            patch_entry_df<K, 1, true>(i, C - 1, h, lo);
+            df_acc_add(acc, h, lo, f11);
+            patch_entry_df<K, 0, true>(i, C - 1, h, lo);
+            df_acc_add(acc, h, lo, f21);
+          }
+          df_acc_add(acc, kyh, kyl, ld(FY, M * M + i));
+          df_acc_add(acc, myh, myl, ld(FY, i));
+          df_acc_add(acc, kzh, kzl, ld(FZ, M * M + i));
+          df_acc_add(acc, mzh, mzl, ld(FZ, i));
+          rd[i] = df_acc_value(acc);
+        }
+        fd_forward_df<K>(rd, yd);
+        float2* R = WB2 + q * Z::WB + M * ln;
+#pragma unroll
+        for (int i = 0; i < M; ++i) R[i] = make_float2(yd[i].hi, yd[i].lo);
+        continue;
+      }
       const T f10 = FX[l * M + j], f20 = FX[M * M + l * M + j];
       const T f11 = FX[FS + l * M + j], f21 = FX[FS + M * M + l * M + j];
       // column 0 (rows up to K-1) or 2K of rows j and l
@@ -411,20 +595,10 @@ __global__ void __launch_bounds__(NT) patch_face_kernel(const __grid_constant__ 
         acc = fma(-my, FY[i], fma(-ky, FY[M * M + i], acc));
         r[i] = fma(-mz, FZ[i], fma(-kz, FZ[M * M + i], acc));
       }
-      if constexpr (DF) {
-        dfv rd[M], yd[M];
+      fd_forward<K>(r, y);
+      T* R = WB + q * Z::WB + M * ln;
 #pragma unroll
-        for (int i = 0; i < M; ++i) rd[i] = df_from_double(r[i]);
-        fd_forward_df<K>(rd, yd);
-        float2* R = WB2 + q * Z::WB + M * ln;
-#pragma unroll
-        for (int i = 0; i < M; ++i) R[i] = make_float2(yd[i].hi, yd[i].lo);
-      } else {
-        fd_forward<K>(r, y);
-        T* R = WB + q * Z::WB + M * ln;
-#pragma unroll
-        for (int i = 0; i < M; ++i) R[i] = y[i];
-      }
+      for (int i = 0; i < M; ++i) R[i] = y[i];
     }
     __syncthreads();
     // ---- local solve by fast diagonalisation (App. A.3), in place in WB ----
@@ -519,7 +693,11 @@ static int face_sweep_impl(const PatchLaunch& pl, T* u, const T* b, const T* din
   using FC = FaceCfg<K, kFaceThreads>;
   using SC = FaceSweepCfg<K>;
   using Z = FaceSweepSmem<K>;
-  auto fk = face_kernel<K, kFaceThreads>;
+  // FP64 problems evaluate the faces in double-float (float-pair fields)
+  auto fk = [] {
+    if constexpr (sizeof(T) == 8) return face_kernel_df<K, kFaceThreads>;
+    else return face_kernel<K, kFaceThreads>;
+  }();
   auto pk = patch_face_kernel<K, SC::NT, SC::PPC, SC::NBUF>;
   static PerDevice<int> per_sm_dev;
   int* const per_sm_p = per_sm_dev.get();
@@ -535,7 +713,11 @@ static int face_sweep_impl(const PatchLaunch& pl, T* u, const T* b, const T* din
   const long long bx = (fg.nf[0] + FC::FX - 1) / FC::FX, by = (fg.nf[1] + FC::FYZ - 1) / FC::FYZ,
                   bz = (fg.nf[2] + FC::FYZ - 1) / FC::FYZ;
   if (bx + by + bz > (1LL << 31) - 1) return GMG_ERR_UNSUPPORTED;
-  fk<<<(unsigned)(bx + by + bz), kFaceThreads, FC::SMEM, s>>>(u, faces, fg, (int)bx, (int)by);
+  if constexpr (sizeof(T) == 8)
+    fk<<<(unsigned)(bx + by + bz), kFaceThreads, FC::SMEM, s>>>(u, reinterpret_cast<float2*>(faces), fg, (int)bx,
+                                                                (int)by);
+  else
+    fk<<<(unsigned)(bx + by + bz), kFaceThreads, FC::SMEM, s>>>(u, faces, fg, (int)bx, (int)by);
   count_launch();
   if (cudaGetLastError() != cudaSuccess) return GMG_ERR_CUDA;
 

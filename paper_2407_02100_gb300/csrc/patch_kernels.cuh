@@ -22,6 +22,7 @@
 
 #include "../../include/gmg.h"
 #include "async.cuh"
+#include "df_convert.h"
 #include "kernels.h"
 
 #ifndef GMG_T
@@ -54,6 +55,17 @@ __constant__ T c_Kc[kCellTotal];
 // transforms of FP64 problems; unused by FP32 problems)
 __constant__ float c_Thi[kTTotal];
 __constant__ float c_Tlo[kTTotal];
+// the two-cell patch matrices split the same way (double-float residual and
+// face terms of FP64 problems)
+__constant__ float c_Mphi[kPatchTotal];
+__constant__ float c_Mplo[kPatchTotal];
+__constant__ float c_Kphi[kPatchTotal];
+__constant__ float c_Kplo[kPatchTotal];
+// and the unit-cell matrices (double-float three-pass operator)
+__constant__ float c_Mchi[kCellTotal];
+__constant__ float c_Mclo[kCellTotal];
+__constant__ float c_Kchi[kCellTotal];
+__constant__ float c_Kclo[kCellTotal];
 
 // band of closure row c (1..2k-1) of the two-cell patch matrices
 __host__ __device__ constexpr int band_lo(int c, int K) { return c > K ? K : 0; }
@@ -209,11 +221,14 @@ __device__ __forceinline__ dfv df_mul(dfv a, dfv b) {
   e = __fmaf_rn(a.lo, b.hi, e);
   return df_fast_two_sum(p, e);
 }
+// conversions by integer operations on the bit patterns (df_convert.h): the
+// F2F conversions to and from FP64 run at the FP64 rate
 __device__ __forceinline__ dfv df_from_double(double x) {
-  const float hi = __double2float_rn(x);
-  return {hi, __double2float_rn(x - (double)hi)};
+  dfv r;
+  dfconv::to_df(x, r.hi, r.lo);
+  return r;
 }
-__device__ __forceinline__ double df_to_double(dfv a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double df_to_double(dfv a) { return dfconv::from_df(a.hi, a.lo); }
 
 // Dot2 accumulator: the exact sum of the leading products is s + (the
 // rounding errors of the additions), collected with the products' errors in e
@@ -287,6 +302,49 @@ __device__ __forceinline__ void fd_backward_df(const dfv (&y)[2 * K - 1], dfv (&
 #pragma unroll
   for (int i = 1; i < K; ++i) df_acc_add(e, c_Thi[off_t(K) + c * M + i], c_Tlo[off_t(K) + c * M + i], y[i]);
   x[c] = df_acc_value(e);
+}
+
+// entry (i, j) of the two-cell patch matrix M_p (KIND 0) or K_p (KIND 1) as
+// a float pair, negated with NEG
+template <int K, int KIND, bool NEG = false>
+__device__ __forceinline__ void patch_entry_df(int i, int j, float& hi, float& lo) {
+  constexpr int C = 2 * K + 1;
+  const int o = off_patch(K) + i * C + j;
+  hi = KIND == 0 ? c_Mphi[o] : c_Kphi[o];
+  lo = KIND == 0 ? c_Mplo[o] : c_Kplo[o];
+  if (NEG) {
+    hi = -hi;
+    lo = -lo;
+  }
+}
+
+// acc += (or -= with NEG) sum_j E[i][j] x[j] over the band of closure row
+// i+1 of E = M_p (KIND 0) or K_p (KIND 1), double-float (Dot2)
+template <int K, int KIND, bool NEG = false>
+__device__ __forceinline__ void patch_row_df(int i, const dfv (&x)[2 * K + 1], df_acc& acc) {
+  constexpr int C = 2 * K + 1;
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    if (j >= band_lo(i + 1, K) && j <= band_hi(i + 1, K)) {
+      float h, l;
+      patch_entry_df<K, KIND, NEG>(i, j, h, l);
+      df_acc_add(acc, h, l, x[j]);
+    }
+  }
+}
+
+// the same over the interior columns 1..2K-1 (x[a] at closure column a + 1)
+template <int K, int KIND>
+__device__ __forceinline__ void patch_row_int_df(int i, const dfv (&x)[2 * K - 1], df_acc& acc) {
+  constexpr int M = 2 * K - 1;
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    if (a + 1 >= band_lo(i + 1, K) && a + 1 <= band_hi(i + 1, K)) {
+      float h, l;
+      patch_entry_df<K, KIND>(i, a + 1, h, l);
+      df_acc_add(acc, h, l, x[a]);
+    }
+  }
 }
 
 // double-float FD transform of a shared-memory line (pairs, stride s) in place

@@ -271,6 +271,31 @@ static int upload(int k, const double* Mp, const double* Kp, const double* That,
   }
   e = e == cudaSuccess ? cudaMemcpyToSymbol(c_Thi, thi.data(), thi.size() * sizeof(float), off_t(k) * sizeof(float)) : e;
   e = e == cudaSuccess ? cudaMemcpyToSymbol(c_Tlo, tlo.data(), tlo.size() * sizeof(float), off_t(k) * sizeof(float)) : e;
+  std::vector<float> mhi(M * C), mlo(M * C), khi(M * C), klo(M * C);
+  for (int i = 0; i < M * C; ++i) {
+    mhi[i] = (float)Mp[i];
+    mlo[i] = (float)(Mp[i] - (double)mhi[i]);
+    khi[i] = (float)Kp[i];
+    klo[i] = (float)(Kp[i] - (double)khi[i]);
+  }
+  const size_t po = off_patch(k) * sizeof(float), pb = mhi.size() * sizeof(float);
+  e = e == cudaSuccess ? cudaMemcpyToSymbol(c_Mphi, mhi.data(), pb, po) : e;
+  e = e == cudaSuccess ? cudaMemcpyToSymbol(c_Mplo, mlo.data(), pb, po) : e;
+  e = e == cudaSuccess ? cudaMemcpyToSymbol(c_Kphi, khi.data(), pb, po) : e;
+  e = e == cudaSuccess ? cudaMemcpyToSymbol(c_Kplo, klo.data(), pb, po) : e;
+  const int nc = (k + 1) * (k + 1);
+  std::vector<float> mch(nc), mcl(nc), kch(nc), kcl(nc);
+  for (int i = 0; i < nc; ++i) {
+    mch[i] = (float)Mc[i];
+    mcl[i] = (float)(Mc[i] - (double)mch[i]);
+    kch[i] = (float)Kc[i];
+    kcl[i] = (float)(Kc[i] - (double)kch[i]);
+  }
+  const size_t co = off_cell(k) * sizeof(float), cb = nc * sizeof(float);
+  e = e == cudaSuccess ? cudaMemcpyToSymbol(c_Mchi, mch.data(), cb, co) : e;
+  e = e == cudaSuccess ? cudaMemcpyToSymbol(c_Mclo, mcl.data(), cb, co) : e;
+  e = e == cudaSuccess ? cudaMemcpyToSymbol(c_Kchi, kch.data(), cb, co) : e;
+  e = e == cudaSuccess ? cudaMemcpyToSymbol(c_Kclo, kcl.data(), cb, co) : e;
   return e == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
 }
 
