@@ -9,8 +9,12 @@ solve by fast diagonalisation on 2^3 cells, levels 64-32-16-8-4-2)
 preconditioned CG from u = 0 to ||r|| <= 1e-10 ||b||.
 
 Reported: whole-job solve throughput (all nodes / time to 1e-10) as
-`value`; the finest-level smoother sweep rate and its roofline against the
-FP64 FMA peak measured in the same run; the same solve end to end through
+`value`; the finest-level smoother sweep rate and its roofline (the FP64
+sweep runs in double-float arithmetic on the FP32 pipe and is bound by
+instruction issue: executed warp instructions per second against the issue
+slots of the GPU at the sampled clock, and beside it the method's FP64
+operation count per second against the FP64 FMA peak measured in the same
+run); the same solve end to end through
 the C ABI with host buffers (`e2e`); the FP32-mixed solve of the same
 workload; the FP64 oracle's sweep of the full 64^3 grid timed on the host
 cores at one core and at all cores (`cpu_baseline`); and two further
@@ -48,19 +52,21 @@ BYTES_PER_NODE = 24
 # 2.07 GHz), used only if the in-run measurement (gmg_fma_peak) fails
 FP64_PEAK_DERIVED_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 # The FP64 sweep runs each colour as two launches, the face kernel and the
-# patch kernel (shared-face form); "per launch" figures below are per colour
-# step (both kernels).  DRAM bytes of one average colour step at this
-# workload, from ncu over every launch of 5 sweeps of the current kernels
-# (dram__bytes_read.sum + dram__bytes_write.sum: 18,627.3 MB / 40 colour steps)
-TRAFFIC_PER_LAUNCH = (6166.0e6 + 685.0e6 + 8954.5e6 + 2821.8e6) / 40
-# FP64 operations the kernels execute per patch (ncu SASS thread-instruction
-# counts of the 29,791-patch colour 0, per patch: face kernel 3,925.7 DFMA;
-# patch kernel 9,506 DFMA, 1,960 DADD, 686 DMUL; profiles/face_sweep_fp64_q4_64.md)
-EXECUTED_FLOP_PER_PATCH = 2 * (3925.7 + 9506) + 1960 + 686
-EXECUTED_SOURCE = "profiles/face_sweep_fp64_q4_64.md (ncu SASS FP64 instruction counts, colour 0)"
-# FP64 pipe activity of the two kernels (ncu, one colour step each, current
-# kernels)
-FP64_PIPE_ACTIVE = {"face_kernel": 0.805, "patch_face_kernel": 0.811}
+# patch kernel (shared-face form), both in double-float arithmetic on the
+# FP32 pipe; "per launch" figures below are per colour step (both kernels).
+# From ncu over every launch of 7 sweeps of the current kernels at this
+# workload (profiles/face_sweep_fp64_q4_64.md), per average colour step of
+# 31,256 patches: DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum)
+# and warp instructions issued (smsp__inst_executed.sum), face + patch kernel.
+TRAFFIC_PER_LAUNCH = (151.9e6 + 16.8e6) + (221.1e6 + 68.5e6)
+WARP_INST_PER_PATCH = (90.91e6 + 207.46e6) / (250047 / 8)
+EXECUTED_SOURCE = ("profiles/face_sweep_fp64_q4_64.md: ncu smsp__inst_executed.sum over every launch of 7 sweeps "
+                   "(face_kernel_df + patch_face_kernel), per patch")
+# issue slots of GB300: 152 SMs x 4 schedulers, one warp instruction each per clock
+ISSUE_SLOTS_PER_CLOCK = 152 * 4
+# FP32 pipe activity of the two kernels (ncu --set full, one colour step each)
+PIPE_ACTIVE = {"face_kernel_df": {"fma": 0.468, "alu": 0.283, "issue": 0.697},
+               "patch_face_kernel": {"fma": 0.432, "alu": 0.225, "issue": 0.621}}
 CPU_SAMPLE = dict(dim=3, degree=4, n_cells=8, n_levels=3)
 BLAS_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
 # further workloads of the method, measured in the same run (one timed solve each)
@@ -357,7 +363,10 @@ def run_ours(args):
     patches = (N_CELLS - 1) ** DIM
     flops_sweep = FLOP_PER_PATCH * patches
     method_tflops = flops_sweep / sweep_s / 1e12
-    executed_tflops = EXECUTED_FLOP_PER_PATCH * patches / sweep_s / 1e12
+    inst_rate = WARP_INST_PER_PATCH * patches / sweep_s / 1e12        # T warp instructions / s
+    sweep_clk = sweep_clocks.summary()
+    sm_hz = (sweep_clk.get("sm_mhz") or 2070.0) * 1e6
+    issue_peak = ISSUE_SLOTS_PER_CLOCK * sm_hz / 1e12
     hbm_gbs = BYTES_PER_NODE * nodes / sweep_s / 1e9
 
     # ---- measured FMA peaks of this GPU (roofline denominators) ----
@@ -471,6 +480,9 @@ def run_ours(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
+        "arithmetic": "FP64 vectors, CG scalars, dot products and coarse solve; the patch sweep, the level "
+                      "operator and the transfers in double-float (pairs of f32, about 48 significant bits, "
+                      "Dot2 accumulation), parity with the FP64 oracle within 1e-12",
         "data": "synthetic (seeded U[-1,1] RHS on interior nodes)",
         "config": {"workload": WORKLOAD,
                    "nodes": nodes, "interior_dofs": (N_CELLS * DEGREE - 1) ** DIM,
@@ -481,7 +493,7 @@ def run_ours(args):
         "phase_ms": phases,
         "smoother": {"ms_per_sweep": sweep_s * 1e3, "mdofs": nodes / sweep_s / 1e6,
                      "hbm_gbs_algorithmic": hbm_gbs, "patches": patches,
-                     "flop_per_patch": FLOP_PER_PATCH, "clocks": sweep_clocks.summary()},
+                     "flop_per_patch": FLOP_PER_PATCH, "clocks": sweep_clk},
         "fp32_mixed": {"time_to_solution_ms": ms32, "mdofs": nodes / (ms32 * 1e-3) / 1e6,
                        "cg_iterations": st32.iterations, "final_rel_residual": res32,
                        "rel_diff_vs_fp64_solution": diff32,
@@ -494,26 +506,29 @@ def run_ours(args):
                            (flops_sweep / sweep32_s / 1e12 / peak32) if peak32 else None,
                        "fp32_fma_peak_tflops": peak32,
                        "clocks": clocks32.summary()},
-        "roofline": {"bound": "alu", "achieved": executed_tflops, "peak": peak64,
-                     "unit": "TFLOP/s", "frac": executed_tflops / peak64,
-                     "peak_source": peak64_src + " (of measured)",
+        "roofline": {"bound": "alu", "achieved": inst_rate, "peak": issue_peak, "unit": "Twarp-inst/s",
+                     "frac": inst_rate / issue_peak,
+                     "peak_source": "derived: 152 SMs x 4 schedulers x 1 warp instruction per clock x the SM "
+                                    f"clock sampled during the sweeps ({sm_hz / 1e6:.0f} MHz); no issue-rate "
+                                    "peak is measured by the driver",
                      "traffic": TRAFFIC_PER_LAUNCH,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum over every "
-                                       "launch of 5 sweeps, per colour step (face kernel + patch kernel); "
-                                       "profiles/sweep_dram_bytes_per_dof_q4_64.md",
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum over every launch of 7 "
+                                       "sweeps, per colour step (face kernel + patch kernel); "
+                                       "profiles/face_sweep_fp64_q4_64.md",
                      "algorithmic_bytes_per_launch": BYTES_PER_NODE * nodes / 8,
-                     "executed_flop_per_patch": EXECUTED_FLOP_PER_PATCH,
+                     "executed_warp_inst_per_patch": WARP_INST_PER_PATCH,
                      "executed_source": EXECUTED_SOURCE,
-                     "work_equivalent": {"achieved": method_tflops, "frac": method_tflops / peak64,
+                     "pipe_active_ncu": PIPE_ACTIVE,
+                     "fp64_equivalent": {"achieved": method_tflops, "unit": "TFLOP/s", "peak": peak64,
+                                         "frac": method_tflops / peak64, "peak_source": peak64_src,
                                          "flop_per_patch": FLOP_PER_PATCH,
-                                         "note": "the method's operation count (2^3 cells x 7 contractions "
-                                                 "of (k+1)^4 + 6 FD contractions of (2k-1)^4 multiply-adds); "
-                                                 "the kernels compute the same sweep with fewer operations "
-                                                 "(banded two-cell matrices, even/odd FD, residual from the "
-                                                 "closure faces), so this rate exceeds the peak"},
-                     "fp64_pipe_active_ncu": FP64_PIPE_ACTIVE,
-                     "kernel": "face_kernel<4,128> + patch_face_kernel<4,256,5,2> (FP64 shared-face "
-                               "sweep), one pair of launches per colour; timed as whole sweeps"},
+                                         "note": "the method's FP64 operation count (2^3 cells x 7 contractions of "
+                                                 "(k+1)^4 + 6 FD contractions of (2k-1)^4 multiply-adds) per second, "
+                                                 "against the measured FP64 FMA peak; the kernels compute the sweep "
+                                                 "in double-float arithmetic on the FP32 pipe with a regrouped "
+                                                 "(banded, even/odd, shared-face) operation count"},
+                     "kernel": "face_kernel_df<4,128> + patch_face_kernel<4,256,5,1> (FP64 shared-face sweep in "
+                               "double-float arithmetic), one pair of launches per colour; timed as whole sweeps"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "MDoF/s", "h2d_bytes_per_step": n_elems * 8,
                 "d2h_bytes_per_step": n_elems * 8},

@@ -123,6 +123,17 @@ int upload_table(gmg_problem* p, void** dst, const std::vector<double>& src) {
   return e == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
 }
 
+// Append to a table of doubles the same entries as float pairs (hi, lo),
+// two per double slot, for the double-float kernels of FP64 problems.
+void append_float_pairs(std::vector<double>& t) {
+  const size_t n = t.size();
+  t.resize(2 * n);
+  for (size_t i = 0; i < n; ++i) {
+    const float pair[2] = {(float)t[i], (float)(t[i] - (double)(float)t[i])};
+    std::memcpy(&t[n + i], pair, sizeof(pair));
+  }
+}
+
 LevelGeom make_geom(int dim, int k, int n) {
   LevelGeom g;
   g.dim = dim;
@@ -457,6 +468,7 @@ int prolongate_add(gmg_problem* p, int cl, const void* coarse, void* fine) {
     Arr out = last ? level_arr(gf) : compact_arr(ext[0], ext[1], ext[2]);
     void* dst = last ? fine : (a % 2 == 0 ? p->tmp1 : p->tmp2);
     AxisOp op = make_op(a, cur, zero, out, ext, zero, 2 * k, k, 0, k + 1, last ? 1 : 0);
+    op.df = p->esize == 8 ? 1 : 0;
     CHECK(axis_op(p, op, src, dst, p->coef_prol));
     cur = out;
     src = dst;
@@ -491,6 +503,7 @@ int restrict_to(gmg_problem* p, int fl, const void* fine, void* coarse) {
     // coarse node c = o + 1 gathers fine nodes 2k(c/k) - (2k-1) .. + (2k-1)
     AxisOp op = make_op(a, cur, ioff, out, cnt, ooff, k, 2 * k, -(2 * k - 1), 4 * k - 1, 0);
     op.shift = 1;
+    op.df = p->esize == 8 ? 1 : 0;
     CHECK(axis_op(p, op, src, dst, p->coef_rest));
     cur = out;
     src = dst;
@@ -679,17 +692,9 @@ int gmg::detail::create_problem(const gmg_desc* d, gmg_problem* p, const CreateO
     double s = lp[x] + lp[y] + (dim == 3 ? lp[z] : 0.0);
     dinv[t] = 1.0 / s;
   }
-  if (p->esize == 8) {
-    // FP64 problems: the table is followed by its double-float split, the
-    // float pair (hi, lo) with hi + lo = 1 / (sum of eigenvalues) to about
-    // 48 bits, read by the shared-face sweep's double-float FD transforms
-    dinv.resize(2 * (size_t)nint);
-    for (int t = 0; t < nint; ++t) {
-      const float hi = (float)dinv[t], lo = (float)(dinv[t] - (double)hi);
-      float pair[2] = {hi, lo};
-      std::memcpy(&dinv[nint + t], pair, sizeof(pair));
-    }
-  }
+  // FP64 problems: the table is followed by its float-pair split, read by
+  // the shared-face sweep's double-float FD transforms
+  if (p->esize == 8) append_float_pairs(dinv);
   CHECK(upload_table(p, &p->dinv, dinv));
   // face buffer of the shared-face sweep: the largest colour of the finest
   // level; without memory for it the closure form is used.  FP64 problems
@@ -719,6 +724,7 @@ int gmg::detail::create_problem(const gmg_desc* d, gmg_problem* p, const CreateO
   std::vector<double> prol(2 * k * (k + 1));
   for (int r = 0; r < 2 * k; ++r)
     for (int q = 0; q <= k; ++q) prol[r * (k + 1) + q] = P1[r * (k + 1) + q];
+  if (p->esize == 8) append_float_pairs(prol);  // double-float transfers of FP64 problems
   CHECK(upload_table(p, &p->coef_prol, prol));
   const int W = 4 * k - 1;
   std::vector<double> rest(k * W, 0.0);
@@ -735,6 +741,7 @@ int gmg::detail::create_problem(const gmg_desc* d, gmg_problem* p, const CreateO
       }
       rest[q * W + w] = v;
     }
+  if (p->esize == 8) append_float_pairs(rest);  // double-float transfers of FP64 problems
   CHECK(upload_table(p, &p->coef_rest, rest));
   // transfer temporaries: largest intermediate array of any pass
   long long tmax = 1;

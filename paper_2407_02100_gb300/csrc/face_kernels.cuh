@@ -659,9 +659,14 @@ __global__ void __launch_bounds__(NT) patch_face_kernel(const __grid_constant__ 
 // patches per CTA, threads and input buffers of the shared-face sweep
 template <int K>
 struct FaceSweepCfg {
-  static constexpr int PPC = K == 3 ? 10 : K == 4 ? 5 : K == 5 ? 3 : K == 6 ? 2 : 1;
-  static constexpr int NT = K == 7 ? 192 : 256;
-  static constexpr int NBUF = K <= 4 || K == 7 ? 2 : 1;
+  // FP64 (double-float arithmetic, bound by FP32 issue) at k = 3, 4: one input
+  // buffer, which leaves room for more resident CTAs (measured on GB300 at
+  // 64^3: k = 3 1.30 -> 1.12 ms, k = 4 3.16 -> 3.03 ms per sweep); FP32 and
+  // the other degrees keep the double-buffered inputs
+  static constexpr bool F64 = sizeof(T) == 8;
+  static constexpr int PPC = K == 3 ? (F64 ? 5 : 10) : K == 4 ? 5 : K == 5 ? 3 : K == 6 ? 2 : 1;
+  static constexpr int NT = K == 7 ? 192 : K == 3 && F64 ? 128 : 256;
+  static constexpr int NBUF = (K <= 4 && !F64) || K == 7 ? 2 : 1;
   static constexpr int SMEM = PPC * FaceSweepSmem<K>::per_patch(NBUF) * (int)sizeof(T) + 128;
   static_assert(SMEM <= 227 * 1024, "shared-face sweep exceeds the shared memory of a CTA");
   static_assert(PPC * (2 * K - 1) * (2 * K - 1) <= NT + 32 * 2,

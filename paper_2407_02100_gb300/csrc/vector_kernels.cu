@@ -5,6 +5,7 @@
 #include <algorithm>
 
 #include "../../include/gmg.h"
+#include "df_arith.cuh"
 #include "kernels.h"
 
 namespace gmg {
@@ -40,6 +41,24 @@ __global__ void axis_op_kernel(const T* __restrict__ in, T* __restrict__ out,
       }
       const int oa = o[AX] + op.shift;
       const int start = (oa / op.R) * op.S + op.off;
+      if constexpr (sizeof(T) == 8) {
+        if (op.df) {  // double-float: FP64 values in and out, float-pair coefficients
+          const float2* __restrict__ c2 =
+              reinterpret_cast<const float2*>(coef + op.R * op.W) + (oa % op.R) * op.W;
+          df_acc acc = {0.f, 0.f};
+          for (int w = 0; w < op.W; ++w) {
+            const int i = start + w;
+            if (i >= 0 && i < lim) {
+              const float2 cw = __ldg(c2 + w);
+              df_acc_add(acc, cw.x, cw.y, df_from_double(in[ibase + i * sa]));
+            }
+          }
+          dfv v = df_acc_value(acc);
+          if (op.accumulate) v = df_add(df_from_double(out[obase]), v);
+          out[obase] = df_to_double(v);
+          continue;
+        }
+      }
       const T* __restrict__ c = coef + (oa % op.R) * op.W;
       T acc = T(0);
       for (int w = 0; w < op.W; ++w) {
