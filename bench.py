@@ -480,8 +480,8 @@ def run_ours(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
-        "arithmetic": "FP64 vectors, CG scalars, dot products and coarse solve; the patch sweep, the level "
-                      "operator and the transfers in double-float (pairs of f32, about 48 significant bits, "
+        "arithmetic": "FP64 vectors, CG scalars, dot products, transfers and coarse solve; the patch sweep "
+                      "and the level operator in double-float (pairs of f32, about 48 significant bits, "
                       "Dot2 accumulation), parity with the FP64 oracle within 1e-12",
         "data": "synthetic (seeded U[-1,1] RHS on interior nodes)",
         "config": {"workload": WORKLOAD,

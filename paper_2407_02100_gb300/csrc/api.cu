@@ -468,7 +468,6 @@ int prolongate_add(gmg_problem* p, int cl, const void* coarse, void* fine) {
     Arr out = last ? level_arr(gf) : compact_arr(ext[0], ext[1], ext[2]);
     void* dst = last ? fine : (a % 2 == 0 ? p->tmp1 : p->tmp2);
     AxisOp op = make_op(a, cur, zero, out, ext, zero, 2 * k, k, 0, k + 1, last ? 1 : 0);
-    op.df = p->esize == 8 ? 1 : 0;
     CHECK(axis_op(p, op, src, dst, p->coef_prol));
     cur = out;
     src = dst;
@@ -503,7 +502,6 @@ int restrict_to(gmg_problem* p, int fl, const void* fine, void* coarse) {
     // coarse node c = o + 1 gathers fine nodes 2k(c/k) - (2k-1) .. + (2k-1)
     AxisOp op = make_op(a, cur, ioff, out, cnt, ooff, k, 2 * k, -(2 * k - 1), 4 * k - 1, 0);
     op.shift = 1;
-    op.df = p->esize == 8 ? 1 : 0;
     CHECK(axis_op(p, op, src, dst, p->coef_rest));
     cur = out;
     src = dst;
@@ -724,7 +722,6 @@ int gmg::detail::create_problem(const gmg_desc* d, gmg_problem* p, const CreateO
   std::vector<double> prol(2 * k * (k + 1));
   for (int r = 0; r < 2 * k; ++r)
     for (int q = 0; q <= k; ++q) prol[r * (k + 1) + q] = P1[r * (k + 1) + q];
-  if (p->esize == 8) append_float_pairs(prol);  // double-float transfers of FP64 problems
   CHECK(upload_table(p, &p->coef_prol, prol));
   const int W = 4 * k - 1;
   std::vector<double> rest(k * W, 0.0);
@@ -741,7 +738,6 @@ int gmg::detail::create_problem(const gmg_desc* d, gmg_problem* p, const CreateO
       }
       rest[q * W + w] = v;
     }
-  if (p->esize == 8) append_float_pairs(rest);  // double-float transfers of FP64 problems
   CHECK(upload_table(p, &p->coef_rest, rest));
   // transfer temporaries: largest intermediate array of any pass
   long long tmax = 1;

@@ -1,5 +1,5 @@
-// Double-float arithmetic shared by the FP64 kernels (sweep, operator,
-// transfers).  Included by patch_kernels.cuh and vector_kernels.cu.
+// Double-float arithmetic shared by the FP64 kernels (sweep, operator).
+// Included by patch_kernels.cuh.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -8,7 +8,7 @@
 namespace gmg {
 
 // GB300 issues FP64 fused multiply-adds at about 1/74 of its FP32 rate, so
-// the arithmetic of FP64 problems (sweep, operator, transfers) runs in
+// the arithmetic of FP64 problems' sweep and level operator runs in
 // double-float arithmetic on the FP32 pipe: a value is the unevaluated sum
 // hi + lo of two floats (about 48 significant bits).  A product's rounding error is recovered
 // exactly with one fmaf (TwoProd, after Dekker), a sum's with Knuth's

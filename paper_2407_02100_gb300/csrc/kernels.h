@@ -90,9 +90,6 @@ struct AxisOp {
   int R, S, off, W;
   int shift;
   int accumulate;
-  // FP64 in and out, double-float arithmetic: the coefficient table of R x W
-  // doubles is followed by the same entries as float pairs (hi, lo)
-  int df = 0;
 };
 
 // Device flag of the bounded device-side waits (TMA gathers, tensor-core

@@ -5,7 +5,6 @@
 #include <algorithm>
 
 #include "../../include/gmg.h"
-#include "df_arith.cuh"
 #include "kernels.h"
 
 namespace gmg {
@@ -20,18 +19,22 @@ inline int grid_for(long long n, int threads) {
 }
 
 // out[o + out_off] (+)= sum_w coef[(o_ax % R) W + w] in[(o_ax / R) S + off + w]
-// with one thread per output element: threads along x (loads and stores
-// along the contiguous axis coalesce), blocks along y and z (grid-strided
-// beyond the grid limits), the contracted axis AX a template parameter.
+// with one thread per output element: the (x, y) plane is flattened over
+// the threads (x fastest, so loads and stores along the contiguous axis
+// coalesce and no block runs mostly idle), z planes over grid.y
+// (grid-strided beyond its limit), the contracted axis AX a template
+// parameter.
 template <typename T, int AX>
 __global__ void axis_op_kernel(const T* __restrict__ in, T* __restrict__ out,
                                const T* __restrict__ coef, AxisOp op) {
-  const int o0 = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o0 >= op.cnt[0]) return;
+  // one thread per output of a (x, y) plane, planes z strided over grid.y
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)op.cnt[0] * op.cnt[1]) return;
+  const int o0 = (int)(t % op.cnt[0]), o1 = (int)(t / op.cnt[0]);
   const long long sa = op.in_stride[AX];
   const int lim = op.in_dim[AX];
-  for (int o2 = blockIdx.z; o2 < op.cnt[2]; o2 += gridDim.z)
-    for (int o1 = blockIdx.y; o1 < op.cnt[1]; o1 += gridDim.y) {
+  for (int o2 = blockIdx.y; o2 < op.cnt[2]; o2 += gridDim.y) {
+    {
       const int o[3] = {o0, o1, o2};
       long long ibase = 0, obase = 0;
 #pragma unroll
@@ -41,24 +44,6 @@ __global__ void axis_op_kernel(const T* __restrict__ in, T* __restrict__ out,
       }
       const int oa = o[AX] + op.shift;
       const int start = (oa / op.R) * op.S + op.off;
-      if constexpr (sizeof(T) == 8) {
-        if (op.df) {  // double-float: FP64 values in and out, float-pair coefficients
-          const float2* __restrict__ c2 =
-              reinterpret_cast<const float2*>(coef + op.R * op.W) + (oa % op.R) * op.W;
-          df_acc acc = {0.f, 0.f};
-          for (int w = 0; w < op.W; ++w) {
-            const int i = start + w;
-            if (i >= 0 && i < lim) {
-              const float2 cw = __ldg(c2 + w);
-              df_acc_add(acc, cw.x, cw.y, df_from_double(in[ibase + i * sa]));
-            }
-          }
-          dfv v = df_acc_value(acc);
-          if (op.accumulate) v = df_add(df_from_double(out[obase]), v);
-          out[obase] = df_to_double(v);
-          continue;
-        }
-      }
       const T* __restrict__ c = coef + (oa % op.R) * op.W;
       T acc = T(0);
       for (int w = 0; w < op.W; ++w) {
@@ -68,6 +53,7 @@ __global__ void axis_op_kernel(const T* __restrict__ in, T* __restrict__ out,
       if (op.accumulate) out[obase] += acc;
       else out[obase] = acc;
     }
+  }
 }
 
 template <typename T>
@@ -230,8 +216,10 @@ inline int status(int launches = 1) {
 template <typename T>
 int launch_axis_op(const AxisOp& op, const T* in, T* out, const T* coef, cudaStream_t s) {
   if ((long long)op.cnt[0] * op.cnt[1] * op.cnt[2] <= 0) return GMG_OK;
-  const int tx = op.cnt[0] >= 256 ? 256 : op.cnt[0] >= 128 ? 128 : op.cnt[0] >= 64 ? 64 : 32;
-  const dim3 grid((op.cnt[0] + tx - 1) / tx, std::min(op.cnt[1], 65535), std::min(op.cnt[2], 65535));
+  const int tx = 256;
+  const long long plane = (long long)op.cnt[0] * op.cnt[1];
+  if ((plane + tx - 1) / tx > 0x7FFFFFFFLL) return GMG_ERR_UNSUPPORTED;
+  const dim3 grid((unsigned)((plane + tx - 1) / tx), std::min(op.cnt[2], 65535));
   switch (op.axis) {
     case 0: axis_op_kernel<T, 0><<<grid, tx, 0, s>>>(in, out, coef, op); break;
     case 1: axis_op_kernel<T, 1><<<grid, tx, 0, s>>>(in, out, coef, op); break;
