@@ -58,15 +58,15 @@ FP64_PEAK_DERIVED_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 # workload (profiles/face_sweep_fp64_q4_64.md), per average colour step of
 # 31,256 patches: DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum)
 # and warp instructions issued (smsp__inst_executed.sum), face + patch kernel.
-TRAFFIC_PER_LAUNCH = (151.9e6 + 16.8e6) + (221.1e6 + 68.5e6)
-WARP_INST_PER_PATCH = (90.91e6 + 207.46e6) / (250047 / 8)
+TRAFFIC_PER_LAUNCH = (151.86e6 + 16.79e6) + (221.64e6 + 69.60e6)
+WARP_INST_PER_PATCH = (90.91e6 + 212.46e6) / (250047 / 8)
 EXECUTED_SOURCE = ("profiles/face_sweep_fp64_q4_64.md: ncu smsp__inst_executed.sum over every launch of 7 sweeps "
                    "(face_kernel_df + patch_face_kernel), per patch")
 # issue slots of GB300: 152 SMs x 4 schedulers, one warp instruction each per clock
 ISSUE_SLOTS_PER_CLOCK = 152 * 4
 # FP32 pipe activity of the two kernels (ncu --set full, one colour step each)
 PIPE_ACTIVE = {"face_kernel_df": {"fma": 0.468, "alu": 0.283, "issue": 0.697},
-               "patch_face_kernel": {"fma": 0.432, "alu": 0.225, "issue": 0.621}}
+               "patch_face_kernel": {"fma": 0.457, "alu": 0.232, "issue": 0.672}}
 CPU_SAMPLE = dict(dim=3, degree=4, n_cells=8, n_levels=3)
 BLAS_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
 # further workloads of the method, measured in the same run (one timed solve each)
