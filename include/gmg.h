@@ -209,6 +209,36 @@ int gmg_vcycle(gmg_problem* p, void* x, const void* b);
 int cg_gmg_solve(gmg_problem* p, double* u, const double* b, double rtol, int max_it,
                  gmg_solve_stats* stats);
 
+/* ---- Autotuning (result-neutral choices timed on the GPU) -----------------
+ * gmg_set_operator_tile: the tile shape of the operator kernel for 3D
+ * problems of degree 3, 4 or 7 where the level operator is the tile kernel
+ * (FP32 levels, FP64 problems without the three-pass form): 0 the default
+ * shape of the precision and degree, 1 cubes, 2 flat 4x4x1 cells, 3 flat
+ * 8x4x1 cells (a shape whose tile exceeds the shared memory of a CTA runs
+ * as the default).  Every shape evaluates each output row by the same sums
+ * in the same order, so results are bit-identical (App. A.1's sum
+ * factorisation, tiled differently).  GMG_ERR_INVALID_ARG for other values.
+ * gmg_autotune: times, on the finest level of p, one smoothing step for the
+ * slab widths 0 (whole colours), 1, 2, 4, 8 and the L2-sized width -1 of
+ * gmg_set_slab_width (only where slab schedules reproduce the whole-colour
+ * sweep bit for bit: constant coefficient, and whole colours in the closure
+ * kernel, i.e. not the shared-face form or the tensor-core sweep), and five
+ * operator applications for each tile shape where the shape is selectable;
+ * keeps the fastest of each, and reports the choice and the times (NULL out
+ * allowed).  Uses the level's internal vectors as scratch (zeroed on
+ * return); synchronises the stream.  GMG_ERR_INVALID_ARG for a null problem
+ * or a batch member (whose finest vectors are the batch's). */
+typedef struct {
+  int slab_width;             /* chosen: 0 whole colours, > 0 width, -1 the L2 rule */
+  int operator_tile;          /* chosen tile shape (see gmg_set_operator_tile) */
+  double sweep_ms;            /* finest-level smoothing step with the choice */
+  double sweep_ms_default;    /* with whole colours */
+  double operator_ms;         /* finest-level operator with the choice */
+  double operator_ms_default; /* with the default tile shape */
+} gmg_tuning;
+int gmg_set_operator_tile(gmg_problem* p, int tile);
+int gmg_autotune(gmg_problem* p, gmg_tuning* out);
+
 /* Per-phase timing of cg_gmg_solve (enable != 0) or none (0, the default).
  * When on, the solver records a pair of CUDA events on the problem's stream
  * around each phase (enum gmg_phase) of every iteration, launches each

@@ -168,6 +168,7 @@ int apply_level(gmg_problem* p, int level, const void* x, void* y, const void* b
   al.g = L.g;
   al.alpha = alpha;
   al.beta = beta;
+  al.tile = p->apply_tile;
   if (p->esize == 8) {
     al.ws = p->op_ws();
     return launch_apply<double>(al, (const double*)x, (double*)y, (const double*)bvec, p->stream);
@@ -663,6 +664,7 @@ int gmg::detail::create_problem(const gmg_desc* d, gmg_problem* p, const CreateO
     lv.n_elems = geom_elems(lv.g);
     lv.h = 1.0 / n;
     if (l == L - 1 && opt.finest_u) {
+      p->finest_borrowed = true;
       lv.u = opt.finest_u;
       lv.b = opt.finest_b;
       lv.r = opt.finest_r;
@@ -863,6 +865,7 @@ int gmg_apply_operator_f64(gmg_problem* p, int level, const double* x, double* y
   al.alpha = op_scale(L);
   al.beta = 0.0;
   al.ws = p->op_ws();
+  al.tile = p->apply_tile;
   return launch_apply<double>(al, x, y, nullptr, p->stream);
 }
 
@@ -949,6 +952,108 @@ int gmg_set_local_solver(gmg_problem* p, int solver) {
     return GMG_OK;
   }
   return GMG_ERR_INVALID_ARG;
+}
+
+int gmg_set_operator_tile(gmg_problem* p, int tile) {
+  if (!p || tile < 0 || tile > 3) return GMG_ERR_INVALID_ARG;
+  drop_cg_graph(p);
+  p->apply_tile = tile;
+  return GMG_OK;
+}
+
+int gmg_autotune(gmg_problem* p, gmg_tuning* out) {
+  if (!p || p->finest_borrowed) return GMG_ERR_INVALID_ARG;
+  drop_cg_graph(p);
+  const int Lf = (int)p->levels.size() - 1;
+  Level& F = p->levels[Lf];
+  cudaStream_t s = p->stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return GMG_ERR_CUDA;
+  int st = GMG_OK;
+  // any data will do for timing; the level's internal vectors are zeroed again below
+  if (cudaMemsetAsync(F.u, 0x3F, F.n_elems * p->esize, s) != cudaSuccess ||
+      cudaMemsetAsync(F.b, 0x3F, F.n_elems * p->esize, s) != cudaSuccess)
+    st = GMG_ERR_CUDA;
+  auto time_ms = [&](auto&& body, int reps, float* ms) -> int {
+    CHECK(body());  // warm-up (sets each kernel up)
+    if (cudaEventRecord(e0, s) != cudaSuccess) return GMG_ERR_CUDA;
+    for (int r = 0; r < reps; ++r) CHECK(body());
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return GMG_ERR_CUDA;
+    if (cudaEventElapsedTime(ms, e0, e1) != cudaSuccess) return GMG_ERR_CUDA;
+    *ms /= (float)reps;
+    return GMG_OK;
+  };
+  gmg_tuning t;
+  std::memset(&t, 0, sizeof(t));
+  t.slab_width = p->slab_width;
+  t.operator_tile = p->apply_tile;
+  // ---- slab width: only where slab schedules give the whole-colour result
+  // bit for bit (the whole-colour sweep uses the closure kernel) ----
+  const bool faces_used = p->faces && p->shared_faces;
+  const bool slabs_ok = !p->varcoef && !faces_used &&
+                        !((p->desc.precision == GMG_FP32_TC || p->desc.precision == GMG_FP32_TF32) &&
+                          tc_supported(F.g.dim, F.g.k));
+  auto sweep = [&]() { return smooth(p, Lf, F.u, F.b, 1, 0); };
+  if (st == GMG_OK && slabs_ok) {
+    const int cand[6] = {0, 1, 2, 4, 8, -1};
+    float best = 0.f;
+    int best_w = 0;
+    for (int i = 0; i < 6 && st == GMG_OK; ++i) {
+      const int W = cand[i];
+      p->slab_width = W;
+      st = build_slabs(p, Lf, slab_width_for(p, F));
+      float ms = 0.f;
+      if (st == GMG_OK) st = time_ms(sweep, 3, &ms);
+      if (i == 0) t.sweep_ms_default = ms;
+      if (st == GMG_OK && (i == 0 || ms < best)) {
+        best = ms;
+        best_w = W;
+      }
+    }
+    p->slab_width = best_w;
+    for (int l = 0; l <= Lf && st == GMG_OK; ++l) st = build_slabs(p, l, slab_width_for(p, p->levels[l]));
+    t.slab_width = best_w;
+    t.sweep_ms = best;
+  } else if (st == GMG_OK) {
+    float ms = 0.f;
+    st = time_ms(sweep, 3, &ms);
+    t.sweep_ms = t.sweep_ms_default = ms;
+  }
+  // ---- tile shape of the operator kernel (3D, degrees 3, 4, 7, where the
+  // level operator is the tile kernel) ----
+  const bool tile_op = !p->varcoef && F.g.dim == 3 && (F.g.k == 3 || F.g.k == 4 || F.g.k == 7) &&
+                       !(p->esize == 8 && p->op_ws());
+  auto apply = [&]() { return apply_level(p, Lf, F.u, F.r, nullptr, op_scale(F), 0.0); };
+  if (st == GMG_OK && tile_op) {
+    float best = 0.f;
+    int best_t = 0;
+    for (int tv = 0; tv <= 3 && st == GMG_OK; ++tv) {
+      p->apply_tile = tv;
+      float ms = 0.f;
+      st = time_ms(apply, 5, &ms);
+      if (tv == 0) t.operator_ms_default = ms;
+      if (st == GMG_OK && (tv == 0 || ms < best)) {
+        best = ms;
+        best_t = tv;
+      }
+    }
+    p->apply_tile = best_t;
+    t.operator_tile = best_t;
+    t.operator_ms = best;
+  } else if (st == GMG_OK) {
+    float ms = 0.f;
+    st = time_ms(apply, 5, &ms);
+    t.operator_ms = t.operator_ms_default = ms;
+  }
+  if (cudaMemsetAsync(F.u, 0, F.n_elems * p->esize, s) != cudaSuccess ||
+      cudaMemsetAsync(F.b, 0, F.n_elems * p->esize, s) != cudaSuccess ||
+      cudaMemsetAsync(F.r, 0, F.n_elems * p->esize, s) != cudaSuccess)
+    st = st == GMG_OK ? GMG_ERR_CUDA : st;
+  if (cudaStreamSynchronize(s) != cudaSuccess) st = st == GMG_OK ? GMG_ERR_CUDA : st;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (out) *out = t;
+  return st;
 }
 
 int gmg_set_phase_timing(gmg_problem* p, int enable) {

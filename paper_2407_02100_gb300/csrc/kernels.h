@@ -68,6 +68,11 @@ struct ApplyLaunch {
   // FP64 3D: four level vectors of workspace (pz * N doubles each) for the
   // halo-free three-pass form, or null for the tile kernel
   void* ws = nullptr;
+  // tile kernel shape in 3D at degrees 3, 4, 7 (gmg_set_operator_tile):
+  // 0 the default of the precision and degree, 1 cubes, 2 flat 4x4x1,
+  // 3 flat 8x4x1 (shapes whose tile does not fit in shared memory fall back
+  // to the default); every shape evaluates the same sums in the same order
+  int tile = 0;
 };
 // whether launch_apply<double> uses the three-pass form in 3D at degree k
 // when given a workspace

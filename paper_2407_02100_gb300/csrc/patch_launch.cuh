@@ -219,10 +219,30 @@ static int apply_cfg(const ApplyLaunch& al, const T* x, T* y, const T* bvec, cud
 // degrees at which the FP64 3D three-pass form beats the tile kernel
 constexpr bool staged_apply_degree(int k) { return k >= 3; }
 
+// a tile variant of the operator if its shared memory fits, else the default
+template <int DIM, int K, int BX, int BY, int BZ, int NT>
+static int apply_variant(const ApplyLaunch& al, const T* x, T* y, const T* bvec, cudaStream_t s) {
+  if constexpr (ApplyDims<DIM, K, BX, BY, BZ>::SMEM_BYTES <= 227 * 1024) {
+    return apply_cfg<DIM, K, BX, BY, BZ, NT>(al, x, y, bvec, s);
+  } else {
+    using Cfg = ApplyCfg<DIM, K>;
+    return apply_cfg<DIM, K, Cfg::BX, Cfg::BY, Cfg::BZ, Cfg::NT>(al, x, y, bvec, s);
+  }
+}
+
 template <int DIM, int K>
 static int apply_impl(const ApplyLaunch& al, const T* x, T* y, const T* bvec, cudaStream_t s) {
   if constexpr (DIM == 3 && sizeof(T) == 8 && staged_apply_degree(K))
     if (al.ws) return staged_apply_impl<K>(al, x, y, bvec, s);
+  if constexpr (DIM == 3 && (K == 3 || K == 4 || K == 7)) {
+    constexpr int BC = ApplyCfg<DIM, K>::BC;
+    switch (al.tile) {
+      case 1: return apply_variant<DIM, K, BC, BC, BC, kApplyThreads>(al, x, y, bvec, s);
+      case 2: return apply_variant<DIM, K, 4, 4, 1, 128>(al, x, y, bvec, s);
+      case 3: return apply_variant<DIM, K, 8, 4, 1, 256>(al, x, y, bvec, s);
+      default: break;
+    }
+  }
   using Cfg = ApplyCfg<DIM, K>;
   static_assert(ApplyDims<DIM, K, Cfg::BX, Cfg::BY, Cfg::BZ>::SMEM_BYTES <= 227 * 1024,
                 "operator tile exceeds the shared memory of a CTA");

@@ -105,6 +105,8 @@ struct gmg_problem {
   // vectors), null where the tile kernel is used
   void* apply_ws = nullptr;
   bool three_pass = true;  // gmg_set_three_pass_operator
+  int apply_tile = 0;      // tile shape of the operator kernel (gmg_set_operator_tile)
+  bool finest_borrowed = false;  // finest u, b, r are slices of a batch's vectors
   void* op_ws() const { return three_pass ? apply_ws : nullptr; }
   // CUDA graph of one outer-CG iteration (V-cycle preconditioner, dot
   // products, direction, FP64 operator, update) for the solution vector

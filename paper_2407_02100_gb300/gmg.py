@@ -36,7 +36,8 @@ EXPORTS = ["gmg_create", "gmg_destroy", "gmg_vector_layout", "gmg_level_info",
            "gmg_learned_corrections", "gmg_mlp_loss_grad", "gmg_tc_status", "gmg_tc_probe",
            "gmg_set_slab_width", "gmg_slab_width", "gmg_set_shared_faces", "gmg_shared_faces",
            "gmg_set_three_pass_operator", "gmg_three_pass_operator", "gmg_exact_patch_solve",
-           "gmg_set_phase_timing", "gmg_fma_peak", "gmg_learned_levels", "gmg_learned_set_levels"]
+           "gmg_set_phase_timing", "gmg_fma_peak", "gmg_learned_levels", "gmg_learned_set_levels",
+           "gmg_set_operator_tile", "gmg_autotune"]
 PHASES = ("smooth", "operator", "transfer", "coarse", "vector")
 GMG_LOCAL_FD_MEAN, GMG_LOCAL_LEARNED = 0, 1
 GMG_SWEEP_COMBINED, GMG_SWEEP_SEPARATED, GMG_SWEEP_BATCHED = 0, 1, 2
@@ -53,6 +54,12 @@ class GmgSolveStats(ctypes.Structure):
                 ("initial_residual", ctypes.c_double), ("final_residual", ctypes.c_double),
                 ("relative_residual", ctypes.c_double), ("residual_history", ctypes.c_double * 64),
                 ("phase_ms", ctypes.c_double * 5)]
+
+
+class GmgTuning(ctypes.Structure):
+    _fields_ = [("slab_width", ctypes.c_int), ("operator_tile", ctypes.c_int),
+                ("sweep_ms", ctypes.c_double), ("sweep_ms_default", ctypes.c_double),
+                ("operator_ms", ctypes.c_double), ("operator_ms_default", ctypes.c_double)]
 
 
 class GmgError(RuntimeError):
@@ -111,6 +118,8 @@ def lib():
             "gmg_fma_peak": [i, ctypes.POINTER(d)],
             "gmg_learned_levels": [vp],
             "gmg_learned_set_levels": [vp, i],
+            "gmg_set_operator_tile": [vp, i],
+            "gmg_autotune": [vp, ctypes.POINTER(GmgTuning)],
             "gmg_smooth_noalloc": [i, i, i, d, vp, vp, i, i, vp],
             "gmg_status_string": [i],
             "gmg_tc_status": [],
@@ -222,6 +231,18 @@ def gmg_fma_peak(precision):
     out = ctypes.c_double()
     _check("gmg_fma_peak", lib().gmg_fma_peak(precision, ctypes.byref(out)))
     return out.value
+
+
+def gmg_set_operator_tile(h, tile):
+    _check("gmg_set_operator_tile", lib().gmg_set_operator_tile(h, tile))
+
+
+def gmg_autotune(h):
+    """Times and keeps the fastest slab width and operator tile shape;
+    returns the GmgTuning record."""
+    t = GmgTuning()
+    _check("gmg_autotune", lib().gmg_autotune(h, ctypes.byref(t)))
+    return t
 
 
 def gmg_set_phase_timing(h, enable):
