@@ -20,7 +20,8 @@ workload; the FP64 oracle's sweep of the full 64^3 grid timed on the host
 cores at one core and at all cores (`cpu_baseline`); and two further
 workloads of the paper's method, each timed once after a warm-up:
 `c3` (3D Q7 48^3, FP64 against FP32 and tensor-core smoothers inside FP64
-CG) and `c5` (3D Q3 64^3 variable coefficient, damped mean-coefficient FD
+CG), `c4` (64 independent Q3 problems, batched against one after another)
+and `c5` (3D Q3 64^3 variable coefficient, damped mean-coefficient FD
 against the learned correction, FP64 and FP32).  `--impl reference` times
 the oracle's PCG alone on a bounded sample.
 
@@ -72,6 +73,7 @@ BLAS_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"
 # further workloads of the method, measured in the same run (one timed solve each)
 C3 = dict(dim=3, degree=7, n_cells=48, seed=0, dist="normal")
 C5 = dict(dim=3, degree=3, n_cells=64, seed=0, sigma=1.0, corr_len=0.1, samples=200000, steps=400)
+C4 = dict(problems=64, degree=3, nmin=16, nmax=96, seed=0)
 WORKLOAD = ("3D Poisson Q4, 64^3 cells, FP64 GMG(V(1,1), 8-colour vertex-patch smoother) "
             "preconditioned CG to 1e-10")
 
@@ -455,6 +457,8 @@ def run_ours(args):
         torch.cuda.empty_cache()
         extra["c5"] = c5_leg(gmg, inputs, torch, local)
         torch.cuda.empty_cache()
+        extra["c4"] = c4_leg(gmg, inputs, torch, local)
+        torch.cuda.empty_cache()
     else:
         P.close()
 
@@ -592,6 +596,61 @@ def c3_leg(gmg, inputs, torch, local):
     for name in ("fp32_mixed", "fp32_tc_mixed"):
         out[name]["speedup_vs_fp64"] = out["fp64"]["time_to_solution_ms"] / out[name]["time_to_solution_ms"]
     return out
+
+
+def c4_leg(gmg, inputs, torch, local):
+    """64 independent 3D Poisson problems, Q3, n drawn from {16, 24, ..., 96}
+    (seeded), N(0,1) right-hand sides: one batched FP32-smoother PCG (one
+    sweep launch per colour over all problems, CUDA-graph V-cycle, FP64 CG
+    per problem, autotuned patches per CTA) against the same problems solved
+    one after another through the single-problem API."""
+    import numpy as np
+    c = C4
+    rng = np.random.default_rng(c["seed"])
+    ns = [int(x) for x in rng.choice(np.arange(c["nmin"], c["nmax"] + 1, 8), size=c["problems"])]
+    nodes = sum((n * c["degree"] + 1) ** 3 for n in ns)
+    B = gmg.Batch(3, c["degree"], ns, precision=gmg.GMG_FP32)
+    rhs = [inputs.random_nodal(3, c["degree"], n, c["seed"] * 1000 + i) for i, n in enumerate(ns)]
+    b = B.pack(rhs, dtype=torch.float64)
+    del rhs
+    u = B.zeros(dtype=torch.float64)
+    ppc = gmg.gmg_batch_autotune(B.h)
+    u.zero_()
+    gmg.gmg_batch_cg_solve(B.h, len(ns), u, b, RTOL, 100)      # warm-up (captures the graph)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    with ClockSampler(local) as ck:
+        u.zero_()
+        e0.record(stream)
+        _, its, res = gmg.gmg_batch_cg_solve(B.h, len(ns), u, b, RTOL, 100)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1)
+    probs = [gmg.Problem(3, c["degree"], n, precision=gmg.GMG_FP32) for n in ns]
+    sols = [P.zeros(dtype=torch.float64) for P in probs]
+    views = [b[B.layouts[i][0]:B.layouts[i][0] + B.layouts[i][1]] for i in range(len(ns))]
+    for P, x, r in zip(probs, sols, views):
+        gmg.cg_gmg_solve(P.h, x, r, RTOL, 100)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for P, x, r in zip(probs, sols, views):
+        x.zero_()
+        gmg.cg_gmg_solve(P.h, x, r, RTOL, 100)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1)
+    diff = max(float(torch.linalg.vector_norm(x - u[B.layouts[i][0]:B.layouts[i][0] + B.layouts[i][1]])
+                     / torch.linalg.vector_norm(x)) for i, x in enumerate(sols))
+    for P in probs:
+        P.close()
+    B.close()
+    return {"workload": "64 independent 3D Poisson problems, Q3, n in {16..96} step 8, N(0,1) RHS, "
+                        "FP32 smoother in FP64 PCG to 1e-10 per problem",
+            "nodes": nodes, "batched_ms": t_batch, "batched_mdofs": nodes / t_batch * 1e3 / 1e6,
+            "sequential_ms": t_seq, "speedup_vs_sequential": t_seq / t_batch, "ppc": ppc,
+            "iterations_min": min(its), "iterations_max": max(its), "rel_residual_max": max(res),
+            "max_rel_diff_vs_sequential": diff, "clocks": ck}
 
 
 def c5_leg(gmg, inputs, torch, local):
