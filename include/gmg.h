@@ -256,9 +256,10 @@ int gmg_set_phase_timing(gmg_problem* p, int enable);
  * on one uniform level of n_cells cells per direction (same layout, colour
  * order and damping semantics as gmg_smooth), in place on the caller's
  * double device vectors u and b, on `stream` (a cudaStream_t).
- * The fast-diagonalisation diagonal lives in a library-owned static device
- * array of (2*8-1)^3 doubles (27 KB, kept on every GPU that loads the
- * library until exit); patches needing more are rejected with
+ * The fast-diagonalisation diagonal (with its float-pair split for the
+ * double-float arithmetic of the FP64 sweep) lives in a library-owned static
+ * device array of 2 (2*8-1)^3 doubles (54 KB, kept on every GPU that loads
+ * the library until exit); patches needing more are rejected with
  * GMG_ERR_INVALID_ARG, as are bad dim/degree/n_cells/damping/pointers.
  * SET-UP: the first call for a (device, degree) pair does that pair's set-up
  * with the device current: it looks the array's address up and copies the

@@ -9,9 +9,11 @@
 //
 // The only device memory the sweep needs beyond the caller's u and b is the
 // fast-diagonalisation diagonal 1/(lambda_x + lambda_y [+ lambda_z]) of the
-// patch.  Here it lives in a file-scope __device__ array sized for the
-// largest supported patch, (2*8-1)^3 doubles = 27 KB, which every GPU that
-// loads the library keeps until the process exits.  Every call writes the
+// patch, followed by the same values as float pairs (hi, lo) for the
+// double-float FD transforms of the FP64 sweep kernel.  Here it lives in a
+// file-scope __device__ array sized for the largest supported patch,
+// 2 (2*8-1)^3 doubles = 54 KB, which every GPU that loads the library keeps
+// until the process exits.  Every call writes the
 // part of it that its degree uses with a small kernel on the caller's stream
 // (the eigenvalues travel as a kernel argument), then launches the colours.
 //
@@ -37,7 +39,7 @@ namespace {
 constexpr int kNoAllocMaxDiag = 15 * 15 * 15;  // (2k-1)^3 for the largest degree k = 8
 constexpr int kMaxM = 15;                       // 2k-1 for k = 8
 
-__device__ __align__(256) double g_fd_diag[kNoAllocMaxDiag];
+__device__ __align__(256) double g_fd_diag[2 * kNoAllocMaxDiag];
 
 // 1D eigenvalues of the two-cell patch pencil K T = M T Lambda (App. A.3)
 struct Lambda1d {
@@ -45,11 +47,16 @@ struct Lambda1d {
 };
 
 // diag[t] = 1 / (lambda_x + lambda_y [+ lambda_z]) for the interior index t
-// of an m^dim patch (x fastest)
+// of an m^dim patch (x fastest), and after the nint doubles the same values
+// as float pairs (hi, lo), one pair per double slot
 __global__ void fill_fd_diag_kernel(double* __restrict__ diag, Lambda1d lam, int m, int dim, int nint) {
+  float2* const pairs = reinterpret_cast<float2*>(diag + nint);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nint; t += gridDim.x * blockDim.x) {
     const int x = t % m, y = (t / m) % m, z = t / (m * m);
-    diag[t] = 1.0 / (lam.v[x] + lam.v[y] + (dim == 3 ? lam.v[z] : 0.0));
+    const double v = 1.0 / (lam.v[x] + lam.v[y] + (dim == 3 ? lam.v[z] : 0.0));
+    diag[t] = v;
+    const float hi = (float)v;
+    pairs[t] = make_float2(hi, (float)(v - (double)hi));
   }
 }
 

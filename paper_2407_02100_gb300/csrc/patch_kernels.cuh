@@ -388,6 +388,9 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
   // (FP32 keeps the correction form: recomputing the interior would cost
   // a factor cond(A_j) in single precision.)
   constexpr bool EXACT = sizeof(T) == 8 && DIM == 3;
+  // FP64: the arithmetic runs in double-float on the FP32 pipe (the work
+  // buffers hold float pairs; the FD diagonal's pairs follow it in dinv)
+  constexpr bool DF = sizeof(T) == 8;
   using Z = SweepSmem<DIM, K, TMA>;
   constexpr int C = Z::C, M = Z::M, XU = Z::XU, XB = Z::XB;
   constexpr int LINES = DIM == 3 ? M * M : M;  // interior lines per axis
@@ -397,6 +400,11 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
                                           : smem_raw);  // [NBUF][PPC][IN]
   T* const WA = IN0 + NBUF * PPC * Z::IN;              // [PPC][WA]
   T* const WB = WA + PPC * Z::WA;                      // [PPC][WB]
+  float2* const WA2 = reinterpret_cast<float2*>(WA);   // DF views (same element size)
+  float2* const WB2 = reinterpret_cast<float2*>(WB);
+  const float2* const dinv_df = reinterpret_cast<const float2*>(dinv + Z::NINT);
+  auto ldf = [](const float2 v) -> dfv { return {v.x, v.y}; };
+  auto stf = [](const dfv v) -> float2 { return make_float2(v.hi, v.lo); };
   __shared__ long long s_origin[2][PPC];
   __shared__ int s_coord[2][PPC][3];   // closure origin (lattice coordinates), TMA gather
   __shared__ int s_nvalid[2];
@@ -563,6 +571,44 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
           const int l = x + C * y;
           const T* U = IN + q * Z::IN + ushift(cur, q) + uo(x, y, 0);
           T* B = WB + q * Z::WB;
+          if constexpr (DF) {
+            float2* B2 = WB2 + q * Z::WB;
+            if (lp < CI * CI) {
+              const dfv u0 = df_from_double(U[0]), uc = df_from_double(U[(C - 1) * C * XU]);
+#pragma unroll
+              for (int i = 0; i < M; ++i) {
+                df_acc a = {0.f, 0.f}, b = {0.f, 0.f};
+                float h, lo;
+                if (band_lo(i + 1, K) == 0) {
+                  patch_entry_df<K, 0>(i, 0, h, lo);
+                  df_acc_add(a, h, lo, u0);
+                  patch_entry_df<K, 1>(i, 0, h, lo);
+                  df_acc_add(b, h, lo, u0);
+                }
+                if (band_hi(i + 1, K) == 2 * K) {
+                  patch_entry_df<K, 0>(i, C - 1, h, lo);
+                  df_acc_add(a, h, lo, uc);
+                  patch_entry_df<K, 1>(i, C - 1, h, lo);
+                  df_acc_add(b, h, lo, uc);
+                }
+                B2[l + i * C * C] = stf(df_acc_value(a));
+                B2[C * C * M + l + i * C * C] = stf(df_acc_value(b));
+              }
+            } else {
+              dfv xv[C];
+#pragma unroll
+              for (int j = 0; j < C; ++j) xv[j] = df_from_double(U[j * C * XU]);
+#pragma unroll
+              for (int i = 0; i < M; ++i) {
+                df_acc a = {0.f, 0.f}, b = {0.f, 0.f};
+                patch_row_df<K, 0>(i, xv, a);
+                patch_row_df<K, 1>(i, xv, b);
+                B2[l + i * C * C] = stf(df_acc_value(a));
+                B2[C * C * M + l + i * C * C] = stf(df_acc_value(b));
+              }
+            }
+            continue;
+          }
           if (lp < CI * CI) {
             const T u0 = U[0], uc = U[(C - 1) * C * XU];
 #pragma unroll
@@ -603,6 +649,26 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
         T* A = WA + q * Z::WA;
         const T* B = WB + q * Z::WB;
         const int x0 = l % C, z = l / C;
+        if constexpr (DF) {
+          const float2* B2 = WB2 + q * Z::WB;
+          float2* A2 = WA2 + q * Z::WA;
+          dfv p[C], r[C];
+#pragma unroll
+          for (int j = 0; j < C; ++j) {
+            p[j] = ldf(B2[x0 + j * C + z * C * C]);
+            r[j] = ldf(B2[C * C * M + x0 + j * C + z * C * C]);
+          }
+#pragma unroll
+          for (int i = 0; i < M; ++i) {
+            df_acc a = {0.f, 0.f}, b = {0.f, 0.f};
+            patch_row_df<K, 0>(i, p, a);
+            patch_row_df<K, 1>(i, p, b);
+            patch_row_df<K, 0>(i, r, b);
+            A2[x0 + i * C + z * C * M] = stf(df_acc_value(a));
+            A2[C * M * M + x0 + i * C + z * C * M] = stf(df_acc_value(b));
+          }
+          continue;
+        }
         T p[C], r[C];
 #pragma unroll
         for (int j = 0; j < C; ++j) {
@@ -622,6 +688,21 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
         const int q = idx / C, l = idx % C;
         const T* U = IN + q * Z::IN + ushift(cur, q) + l;
         T* A = WA + q * Z::WA;
+        if constexpr (DF) {
+          float2* A2 = WA2 + q * Z::WA;
+          dfv xv[C];
+#pragma unroll
+          for (int j = 0; j < C; ++j) xv[j] = df_from_double(U[j * XU]);
+#pragma unroll
+          for (int i = 0; i < M; ++i) {
+            df_acc a = {0.f, 0.f}, b = {0.f, 0.f};
+            patch_row_df<K, 0>(i, xv, a);
+            patch_row_df<K, 1>(i, xv, b);
+            A2[l + i * C] = stf(df_acc_value(a));
+            A2[C * M + l + i * C] = stf(df_acc_value(b));
+          }
+          continue;
+        }
         T x[C];
 #pragma unroll
         for (int j = 0; j < C; ++j) x[j] = U[j * XU];
@@ -644,6 +725,35 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
       // interior row l of b: x = 0..M-1 at (y, z) = (l % M, l / M) (3D) or y = l (2D)
       const T* Bq = IN + q * Z::IN + Z::NCLO + (TMA ? ushift(cur, q) + 1 : 0) +
                     (DIM == 3 ? bo(0, l % M, l / M) : bo(0, l, 0));
+      if constexpr (DF) {
+        const float2* X2 = WA2 + q * Z::WA;
+        const float sbf = (float)ec.sb;  // h^{2-d}: n in 3D, 1 in 2D, exact in float
+        dfv rd[M], yd[M];
+        if (mode == 0) {
+          dfv a1[C], a2[C];
+#pragma unroll
+          for (int j = 0; j < C; ++j) {
+            a1[j] = ldf(X2[j + C * l]);
+            a2[j] = ldf(X2[PLANE + j + C * l]);
+          }
+#pragma unroll
+          for (int i = 0; i < M; ++i) {
+            const dfv bb = df_mul(df_from_double(Bq[i]), {sbf, 0.f});
+            df_acc acc = {bb.hi, bb.lo};
+            patch_row_df<K, 1, true>(i, a1, acc);
+            patch_row_df<K, 0, true>(i, a2, acc);
+            rd[i] = df_acc_value(acc);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < M; ++i) rd[i] = df_mul(df_from_double(Bq[i]), {sbf, 0.f});
+        }
+        fd_forward_df<K>(rd, yd);
+        float2* R2 = WB2 + q * Z::WB + M * l;
+#pragma unroll
+        for (int i = 0; i < M; ++i) R2[i] = stf(yd[i]);
+        continue;
+      }
       T r[M], y[M];
       if (mode == 0) {
         T a1[C], a2[C];
@@ -673,23 +783,27 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
     if (DIM == 3) {
       for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // forward y
         const int q = idx / LINES, l = idx % LINES;
-        fd_smem_line<K, true>(WB + q * Z::WB + (l % M) + (l / M) * M * M, M);
+        if constexpr (DF) fd_smem_line_df<K, true>(WB2 + q * Z::WB + (l % M) + (l / M) * M * M, M);
+        else fd_smem_line<K, true>(WB + q * Z::WB + (l % M) + (l / M) * M * M, M);
       }
       __syncthreads();
       for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // forward z, diagonal, backward z
         const int q = idx / LINES, l = idx % LINES;
-        fd_smem_line_solve<K>(WB + q * Z::WB + l, M * M, dinv + l, M * M);
+        if constexpr (DF) fd_smem_line_solve_df<K>(WB2 + q * Z::WB + l, M * M, dinv_df + l, M * M);
+        else fd_smem_line_solve<K>(WB + q * Z::WB + l, M * M, dinv + l, M * M);
       }
       __syncthreads();
       for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // backward y
         const int q = idx / LINES, l = idx % LINES;
-        fd_smem_line<K, false>(WB + q * Z::WB + (l % M) + (l / M) * M * M, M);
+        if constexpr (DF) fd_smem_line_df<K, false>(WB2 + q * Z::WB + (l % M) + (l / M) * M * M, M);
+        else fd_smem_line<K, false>(WB + q * Z::WB + (l % M) + (l / M) * M * M, M);
       }
       __syncthreads();
     } else {
       for (int idx = threadIdx.x; idx < nvalid * LINES; idx += NT) {  // forward y, diagonal, backward y
         const int q = idx / LINES, l = idx % LINES;
-        fd_smem_line_solve<K>(WB + q * Z::WB + l, M, dinv + l, M);
+        if constexpr (DF) fd_smem_line_solve_df<K>(WB2 + q * Z::WB + l, M, dinv_df + l, M);
+        else fd_smem_line_solve<K>(WB + q * Z::WB + l, M, dinv + l, M);
       }
       __syncthreads();
     }
@@ -701,10 +815,21 @@ __global__ void __launch_bounds__(NT) patch_colour_kernel(const __grid_constant_
       // interior line l of the patch: closure row (y+1, z+1), x = 1..M
       const T* U = IN + q * Z::IN + ushift(cur, q) +
                    (DIM == 3 ? uo(1, l % M + 1, l / M + 1) : uo(1, l + 1, 0));
-      T yv[M], d[M];
+      T d[M];
+      if constexpr (DF) {
+        const float2* R2 = WB2 + q * Z::WB + M * l;
+        dfv yv[M], dd[M];
 #pragma unroll
-      for (int i = 0; i < M; ++i) yv[i] = R[i];
-      fd_backward<K>(yv, d);
+        for (int i = 0; i < M; ++i) yv[i] = ldf(R2[i]);
+        fd_backward_df<K>(yv, dd);
+#pragma unroll
+        for (int i = 0; i < M; ++i) d[i] = df_to_double(dd[i]);
+      } else {
+        T yv[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) yv[i] = R[i];
+        fd_backward<K>(yv, d);
+      }
       const long long row = s_origin[cur][q] + 1 + py * (l % M + 1) + (DIM == 3 ? pz * (l / M + 1) : 0);
 #pragma unroll
       for (int i = 0; i < M; ++i)
