@@ -650,7 +650,7 @@ def c4_leg(gmg, inputs, torch, local):
             "nodes": nodes, "batched_ms": t_batch, "batched_mdofs": nodes / t_batch * 1e3 / 1e6,
             "sequential_ms": t_seq, "speedup_vs_sequential": t_seq / t_batch, "ppc": ppc,
             "iterations_min": min(its), "iterations_max": max(its), "rel_residual_max": max(res),
-            "max_rel_diff_vs_sequential": diff, "clocks": ck}
+            "max_rel_diff_vs_sequential": diff, "clocks": ck.summary()}
 
 
 def c5_leg(gmg, inputs, torch, local):
