@@ -230,9 +230,9 @@ int smooth_colour(gmg_problem* p, int level, void* u, const void* b, int colour)
         p->local_solver == GMG_LOCAL_LEARNED && ((p->corr_levels >> level) & 1u) ? p->corr[level] : nullptr;
     if (p->esize == 8)
       return launch_patch_var<double>(pl, (double*)u, (const double*)b, (const double*)p->coef[level],
-                                      (const double*)p->dinv, corr, p->corr_rank, p->stream);
+                                      (const double*)p->vscale[level], (const double*)p->dinv, corr, p->corr_rank, p->stream);
     return launch_patch_var<float>(pl, (float*)u, (const float*)b, (const float*)p->coef[level],
-                                   (const float*)p->dinv, corr, p->corr_rank, p->stream);
+                                   (const float*)p->vscale[level], (const float*)p->dinv, corr, p->corr_rank, p->stream);
   }
   return launch_colour(p, pl, u, b);
 }
@@ -929,6 +929,31 @@ int gmg_set_coefficient(gmg_problem* p, const double* coef) {
   p->esize = es;
   p->coef.assign(L, nullptr);
   for (int l = 0; l < L; ++l) CHECK(upload_table(p, &p->coef[l], lev[l]));
+  // per interior vertex of each level: the patch's geometric-mean
+  // coefficient abar = exp(mean_c log a_c) over its 2^d cells and the FD
+  // damping theta = min(1, 1.8 abar / max_c a_c)
+  p->vscale.assign(L, nullptr);
+  for (int l = 0; l < L; ++l) {
+    const int n = p->levels[l].g.n, nv = n - 1;
+    const long long ncell = dim == 3 ? (long long)n * n * n : (long long)n * n;
+    const long long nvert = dim == 3 ? (long long)nv * nv * nv : (long long)nv * nv;
+    std::vector<double> lg(ncell), vs(2 * nvert);
+    for (long long c = 0; c < ncell; ++c) lg[c] = std::log(lev[l][c]);
+    for (long long v = 0; v < nvert; ++v) {
+      const int vx = (int)(v % nv), vy = (int)((v / nv) % nv), vz = dim == 3 ? (int)(v / ((long long)nv * nv)) : 0;
+      double s = 0.0, amax = 0.0;
+      for (int o = 0; o < (1 << dim); ++o) {
+        const long long c = (vx + (o & 1)) + (long long)n * ((vy + ((o >> 1) & 1)) +
+                                                          (dim == 3 ? (long long)n * (vz + ((o >> 2) & 1)) : 0));
+        s += lg[c];
+        amax = std::max(amax, lev[l][c]);
+      }
+      const double abar = std::exp(s / (1 << dim));
+      vs[2 * v] = abar;
+      vs[2 * v + 1] = std::min(1.0, 1.8 * abar / amax);
+    }
+    CHECK(upload_table(p, &p->vscale[l], vs));
+  }
   p->coarse_n = (int)nint0;
   p->corr.assign(L, nullptr);
   p->corr_levels = 0;

@@ -148,8 +148,10 @@ int upload_var_tables(int k, const double* Mc, const double* Kc, const double* T
 template <typename T>
 int launch_apply_var(const LevelGeom& g, long long n_elems, const T* x, T* y, const T* bvec,
                      double alpha, double beta, const T* coef, cudaStream_t s);
+// vscale: per interior vertex of the level (x fastest), the patch's
+// geometric-mean coefficient abar and its FD damping theta (two values)
 template <typename T>
-int launch_patch_var(const PatchLaunch& pl, T* u, const T* b, const T* coef, const T* dinv,
+int launch_patch_var(const PatchLaunch& pl, T* u, const T* b, const T* coef, const T* vscale, const T* dinv,
                      const float* corr, int rank, cudaStream_t s);
 
 // x = Ainv b on the interior nodes of a level (Ainv dense FP64, interior

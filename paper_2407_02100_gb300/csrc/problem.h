@@ -84,6 +84,7 @@ struct gmg_problem {
   // cell and level (problem precision), the finest also in FP64 for the CG
   bool varcoef = false;
   std::vector<void*> coef;
+  std::vector<void*> vscale;  // per level: (abar, theta) of every interior vertex's patch
   double* coef64 = nullptr;
   int local_solver = 0;             // GMG_LOCAL_FD_MEAN or GMG_LOCAL_LEARNED
   int corr_rank = 0;

@@ -110,6 +110,115 @@ __device__ __forceinline__ void cell_operator(T* X, T* P, T* Q, T* A1, T* A2, T*
   }
 }
 
+// The same cell operator in double-float arithmetic (FP64 problems): X, P,
+// Q, A1, A2, OUT hold float pairs; the unit-cell matrices as float pairs.
+template <int K, int KIND>
+__device__ __forceinline__ void cell1d_df(int i, const dfv (&x)[K + 1], df_acc& acc) {
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    const int o = off_cell(K) + i * (K + 1) + j;
+    df_acc_add(acc, KIND == 0 ? c_Mchi[o] : c_Kchi[o], KIND == 0 ? c_Mclo[o] : c_Kclo[o], x[j]);
+  }
+}
+
+template <int DIM, int K, int NT>
+__device__ __forceinline__ void cell_operator_df(float2* X, float2* P, float2* Q, float2* A1, float2* A2,
+                                                 float2* OUT, int ncell, int S) {
+  constexpr int E = K + 1;
+  auto ld = [](const float2 v) -> dfv { return {v.x, v.y}; };
+  auto st = [](const df_acc a) -> float2 {
+    const dfv v = df_acc_value(a);
+    return make_float2(v.hi, v.lo);
+  };
+  if (DIM == 3) {
+    for (int idx = threadIdx.x; idx < ncell * E * E; idx += NT) {  // z: P = M_z x, Q = K_z x
+      const int c = idx / (E * E), l = idx % (E * E);
+      dfv v[E];
+#pragma unroll
+      for (int j = 0; j < E; ++j) v[j] = ld(X[c * S + l + j * E * E]);
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        df_acc a = {0.f, 0.f}, b = {0.f, 0.f};
+        cell1d_df<K, 0>(i, v, a);
+        cell1d_df<K, 1>(i, v, b);
+        P[c * S + l + i * E * E] = st(a);
+        Q[c * S + l + i * E * E] = st(b);
+      }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < ncell * E * E; idx += NT) {  // y: A1 = M_y P, A2 = K_y P + M_y Q
+      const int c = idx / (E * E), l = idx % (E * E);
+      const int x0 = l % E, z = l / E;
+      dfv p[E], q[E];
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        p[j] = ld(P[c * S + x0 + j * E + z * E * E]);
+        q[j] = ld(Q[c * S + x0 + j * E + z * E * E]);
+      }
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        df_acc a = {0.f, 0.f}, b = {0.f, 0.f};
+        cell1d_df<K, 0>(i, p, a);
+        cell1d_df<K, 1>(i, p, b);
+        cell1d_df<K, 0>(i, q, b);
+        A1[c * S + x0 + i * E + z * E * E] = st(a);
+        A2[c * S + x0 + i * E + z * E * E] = st(b);
+      }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < ncell * E * E; idx += NT) {  // x: OUT = K_x A1 + M_x A2
+      const int c = idx / (E * E), l = idx % (E * E);
+      dfv a1[E], a2[E];
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        a1[j] = ld(A1[c * S + l * E + j]);
+        a2[j] = ld(A2[c * S + l * E + j]);
+      }
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        df_acc a = {0.f, 0.f};
+        cell1d_df<K, 1>(i, a1, a);
+        cell1d_df<K, 0>(i, a2, a);
+        OUT[c * S + l * E + i] = st(a);
+      }
+    }
+    __syncthreads();
+  } else {
+    for (int idx = threadIdx.x; idx < ncell * E; idx += NT) {  // y: P = M_y x, Q = K_y x
+      const int c = idx / E, l = idx % E;
+      dfv v[E];
+#pragma unroll
+      for (int j = 0; j < E; ++j) v[j] = ld(X[c * S + l + j * E]);
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        df_acc a = {0.f, 0.f}, b = {0.f, 0.f};
+        cell1d_df<K, 0>(i, v, a);
+        cell1d_df<K, 1>(i, v, b);
+        P[c * S + l + i * E] = st(a);
+        Q[c * S + l + i * E] = st(b);
+      }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < ncell * E; idx += NT) {  // x: OUT = K_x P + M_x Q
+      const int c = idx / E, l = idx % E;
+      dfv p[E], q[E];
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        p[j] = ld(P[c * S + l * E + j]);
+        q[j] = ld(Q[c * S + l * E + j]);
+      }
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        df_acc a = {0.f, 0.f};
+        cell1d_df<K, 1>(i, p, a);
+        cell1d_df<K, 0>(i, q, a);
+        OUT[c * S + l * E + i] = st(a);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __device__ __forceinline__ void atomic_add(double* a, double v) { atomicAdd(a, v); }
 __device__ __forceinline__ void atomic_add(float* a, float v) { atomicAdd(a, v); }
 
@@ -120,20 +229,37 @@ __global__ void __launch_bounds__(NT) apply_var_kernel(const T* __restrict__ x, 
   constexpr int E = K + 1;
   constexpr int NE = DIM == 3 ? E * E * E : E * E;
   __shared__ T X[CPC * NE], P[CPC * NE], Q[CPC * NE], A1[CPC * NE], A2[CPC * NE];
+  __shared__ float2 s_sc[CPC];  // alpha a_c of the CTA's cells as float pairs (FP64 problems)
   const int n = g.n, N = g.N;
   const long long ncell = DIM == 3 ? (long long)n * n * n : (long long)n * n;
   for (long long c0 = (long long)blockIdx.x * CPC; c0 < ncell; c0 += (long long)gridDim.x * CPC) {
     const int nc = (int)(ncell - c0 < CPC ? ncell - c0 : CPC);
+    if constexpr (sizeof(T) == 8) {
+      if ((int)threadIdx.x < nc) {
+        const dfv a = df_from_double(alpha * coef[c0 + threadIdx.x]);
+        s_sc[threadIdx.x] = make_float2(a.hi, a.lo);
+      }
+    }
     for (int idx = threadIdx.x; idx < nc * NE; idx += NT) {
       const long long c = c0 + idx / NE;
       const int t = idx % NE;
       const int cx = (int)(c % n), cy = (int)((c / n) % n), cz = DIM == 3 ? (int)(c / ((long long)n * n)) : 0;
       const int lx = t % E, ly = (t / E) % E, lz = DIM == 3 ? t / (E * E) : 0;
       const long long gi = (long long)(cx * K + lx) + g.py * (cy * K + ly) + (DIM == 3 ? g.pz * (cz * K + lz) : 0);
-      X[idx] = x[gi];
+      if constexpr (sizeof(T) == 8) {
+        const dfv v = df_from_double(x[gi]);
+        reinterpret_cast<float2*>(X)[idx] = make_float2(v.hi, v.lo);
+      } else {
+        X[idx] = x[gi];
+      }
     }
     __syncthreads();
-    cell_operator<DIM, K, NT>(X, P, Q, A1, A2, X, nc, NE);  // OUT overwrites X per line (own line only)
+    if constexpr (sizeof(T) == 8)  // double-float cell operator on float pairs
+      cell_operator_df<DIM, K, NT>(reinterpret_cast<float2*>(X), reinterpret_cast<float2*>(P),
+                                   reinterpret_cast<float2*>(Q), reinterpret_cast<float2*>(A1),
+                                   reinterpret_cast<float2*>(A2), reinterpret_cast<float2*>(X), nc, NE);
+    else
+      cell_operator<DIM, K, NT>(X, P, Q, A1, A2, X, nc, NE);  // OUT overwrites X per line (own line only)
     for (int idx = threadIdx.x; idx < nc * NE; idx += NT) {
       const long long c = c0 + idx / NE;
       const int t = idx % NE;
@@ -141,7 +267,12 @@ __global__ void __launch_bounds__(NT) apply_var_kernel(const T* __restrict__ x, 
       const int ix = cx * K + t % E, iy = cy * K + (t / E) % E, iz = DIM == 3 ? cz * K + t / (E * E) : 1;
       if (ix <= 0 || ix >= N - 1 || iy <= 0 || iy >= N - 1 || (DIM == 3 && (iz <= 0 || iz >= N - 1))) continue;
       const long long gi = ix + g.py * iy + (DIM == 3 ? g.pz * iz : 0);
-      atomic_add(y + gi, alpha * coef[c] * X[idx]);
+      if constexpr (sizeof(T) == 8) {
+        const float2 v = reinterpret_cast<const float2*>(X)[idx], a = s_sc[idx / NE];
+        atomic_add(y + gi, df_to_double(df_mul({v.x, v.y}, {a.x, a.y})));
+      } else {
+        atomic_add(y + gi, alpha * coef[c] * X[idx]);
+      }
     }
     __syncthreads();
   }
@@ -169,6 +300,7 @@ __global__ void init_interior_kernel(T* __restrict__ y, const T* __restrict__ b,
 template <int DIM, int K, int NT, bool TMA>
 __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const T* __restrict__ b,
                                                        const T* __restrict__ coef,
+                                                       const T* __restrict__ vscale,
                                                        const T* __restrict__ dinv,
                                                        const float* __restrict__ corr, int rank,
                                                        PatchLaunch pl,
@@ -179,6 +311,9 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
   constexpr int NINT = DIM == 3 ? M * M * M : M * M;
   constexpr int NE = DIM == 3 ? E * E * E : E * E;
   constexpr int NCELL = 1 << DIM;
+  // FP64 problems compute in double-float arithmetic on float pairs held in
+  // the double-sized work buffers; u, b and the coefficients stay FP64
+  constexpr bool DF = sizeof(T) == 8;
   // input slots: closure of u (rows of XU), then interior of b (rows of XB)
   __shared__ __align__(128) T IN[TMA ? 2 : 1][Z::IN];
   __shared__ T R[NINT], RS[NINT];
@@ -186,10 +321,11 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
   __shared__ int s_shift[2];
   __shared__ T X[NCELL * NE], P[NCELL * NE], Q[NCELL * NE], A1[NCELL * NE], A2[NCELL * NE];
   __shared__ T s_coef[NCELL];
+  __shared__ float2 s_coef2[NCELL];
   // the patch's correction block (U then s), prefetched while the residual
   // and the FD solve are computed (rank <= 4)
   __shared__ float s_corr[NINT * 4 + 4];
-  __shared__ T s_abar, s_theta;
+  __shared__ T s_scale, s_theta;
   __shared__ float s_t[8];
   const long long py = pl.g.py, pz = pl.g.pz;
   const int n = pl.g.n;
@@ -264,19 +400,19 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
       const int o0 = threadIdx.x & 1, o1 = (threadIdx.x >> 1) & 1, o2 = (threadIdx.x >> 2) & 1;
       const long long c = (long long)(v0 - 1 + o0) + (long long)n * ((v1 - 1 + o1) + (DIM == 3 ? (long long)n * (v2 - 1 + o2) : 0));
       s_coef[threadIdx.x] = coef[c];
+      if constexpr (DF) {
+        const dfv a = df_from_double(coef[c]);
+        s_coef2[threadIdx.x] = make_float2(a.hi, a.lo);
+      }
     }
     __syncthreads();
     const T* const U = IN[cur] + (TMA ? s_shift[cur] : 0);                   // closure (x, y, z)
     const T* const Bv = IN[cur] + Z::NCLO + (TMA ? s_shift[cur] + 1 : 0);   // interior of b
-    if (threadIdx.x == 0) {
-      T lg = T(0), amax = s_coef[0];
-      for (int c = 0; c < NCELL; ++c) {
-        lg += log(s_coef[c]);
-        amax = max(amax, s_coef[c]);
-      }
-      const T abar = exp(lg / (T)NCELL);
-      s_abar = abar;
-      s_theta = min(T(1), T(1.8) * abar / amax);
+    if (threadIdx.x == 0) {  // the scatter's scale: omega / abar, times theta without the correction
+      const int vid = (v0 - 1) + (n - 1) * ((v1 - 1) + (DIM == 3 ? (n - 1) * (v2 - 1) : 0));
+      const T abar = vscale[2 * (long long)vid], theta = vscale[2 * (long long)vid + 1];
+      s_theta = theta;
+      s_scale = corr ? om / abar : om * theta / abar;
     }
     // ---- local residual: the 2^d cell operators of the patch at once, then
     // R = sum_c a_c [A_c u_c]_interior node by node (cells in ascending order) ----
@@ -284,9 +420,40 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
       const int c = t / NE, l = t % NE;
       const int o0 = c & 1, o1 = (c >> 1) & 1, o2 = (c >> 2) & 1;
       const int x = l % E, y = (l / E) % E, z = DIM == 3 ? l / (E * E) : 0;
-      X[t] = U[uo(o0 * K + x, o1 * K + y, DIM == 3 ? o2 * K + z : 0)];
+      const T v = U[uo(o0 * K + x, o1 * K + y, DIM == 3 ? o2 * K + z : 0)];
+      if constexpr (DF) {
+        const dfv d = df_from_double(v);
+        reinterpret_cast<float2*>(X)[t] = make_float2(d.hi, d.lo);
+      } else {
+        X[t] = v;
+      }
     }
     __syncthreads();
+    float2* const R2 = reinterpret_cast<float2*>(R);
+    float2* const RS2 = reinterpret_cast<float2*>(RS);
+    if constexpr (DF) {
+      float2* const X2 = reinterpret_cast<float2*>(X);
+      cell_operator_df<DIM, K, NT>(X2, reinterpret_cast<float2*>(P), reinterpret_cast<float2*>(Q),
+                                   reinterpret_cast<float2*>(A1), reinterpret_cast<float2*>(A2), X2, NCELL, NE);
+      // R = sum_c a_c [A_c u_c]_interior, then r_ref = h^{2-d} b - R
+      const float sbf = (float)pl.sb;  // an integer power of the cell count, exact in float
+      for (int t = threadIdx.x; t < NINT; t += NT) {
+        const int x = t % M + 1, y = (t / M) % M + 1, z = DIM == 3 ? t / (M * M) + 1 : 0;
+        df_acc acc = {0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < NCELL; ++c) {
+          const int lx = x - (c & 1) * K, ly = y - ((c >> 1) & 1) * K, lz = DIM == 3 ? z - ((c >> 2) & 1) * K : 0;
+          if (lx < 0 || lx > K || ly < 0 || ly > K || lz < 0 || lz > K) continue;
+          const float2 xv = X2[c * NE + lx + E * ly + (DIM == 3 ? E * E * lz : 0)];
+          df_acc_add(acc, s_coef2[c].x, s_coef2[c].y, {xv.x, xv.y});
+        }
+        const dfv bv = df_from_double(Bv[bo(t % M, (t / M) % M, DIM == 3 ? t / (M * M) : 0)]);
+        const dfv r = df_add(df_mul(bv, {sbf, 0.f}), df_neg(df_acc_value(acc)));
+        R2[t] = make_float2(r.hi, r.lo);
+        RS2[t] = R2[t];
+      }
+      __syncthreads();
+    } else {
     cell_operator<DIM, K, NT>(X, P, Q, A1, A2, X, NCELL, NE);
     for (int t = threadIdx.x; t < NINT; t += NT) {
       const int x = t % M + 1, y = (t / M) % M + 1, z = DIM == 3 ? t / (M * M) + 1 : 0;  // closure coords
@@ -307,7 +474,33 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
       R[t] = r;
     }
     __syncthreads();
+    }
     // ---- fast diagonalisation of the constant-coefficient patch ----
+    if constexpr (DF) {
+      for (int a = 0; a < DIM; ++a) {
+        for (int l = threadIdx.x; l < (DIM == 3 ? M * M : M); l += NT) {
+          if (a == 0) fd_smem_line_df<K, true>(R2 + l * M, 1);
+          else if (a == 1) fd_smem_line_df<K, true>(R2 + (l % M) + (DIM == 3 ? (l / M) * M * M : 0), M);
+          else fd_smem_line_df<K, true>(R2 + l, M * M);
+        }
+        __syncthreads();
+      }
+      const float2* const d2 = reinterpret_cast<const float2*>(dinv + NINT);  // the diagonal as float pairs
+      for (int t = threadIdx.x; t < NINT; t += NT) {
+        const float2 a = R2[t], d = __ldg(d2 + t);
+        const dfv v = df_mul({a.x, a.y}, {d.x, d.y});
+        R2[t] = make_float2(v.hi, v.lo);
+      }
+      __syncthreads();
+      for (int a = 0; a < DIM; ++a) {
+        for (int l = threadIdx.x; l < (DIM == 3 ? M * M : M); l += NT) {
+          if (a == 0) fd_smem_line_df<K, false>(R2 + l * M, 1);
+          else if (a == 1) fd_smem_line_df<K, false>(R2 + (l % M) + (DIM == 3 ? (l / M) * M * M : 0), M);
+          else fd_smem_line_df<K, false>(R2 + l, M * M);
+        }
+        __syncthreads();
+      }
+    } else {
     for (int a = 0; a < DIM; ++a) {
       for (int l = threadIdx.x; l < (DIM == 3 ? M * M : M); l += NT) {
         if (a == 0) fd_smem_line<K, true>(R + l * M, 1);
@@ -326,6 +519,7 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
       }
       __syncthreads();
     }
+    }
     // ---- learned rank-R correction U diag(s) U^T r_ref (block prefetched) ----
     if (corr) {
       asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -334,7 +528,7 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
       const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
       for (int q = warp; q < rank; q += NT / 32) {
         float acc = 0.f;
-        for (int i = lane; i < NINT; i += 32) acc += Up[i * rank + q] * (float)RS[i];
+        for (int i = lane; i < NINT; i += 32) acc += Up[i * rank + q] * (DF ? RS2[i].x : (float)RS[i]);
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) s_t[q] = acc * Up[NINT * rank + q];
       }
@@ -342,16 +536,27 @@ __global__ void __launch_bounds__(NT) patch_var_kernel(T* __restrict__ u, const 
       for (int i = threadIdx.x; i < NINT; i += NT) {
         float acc = 0.f;
         for (int q = 0; q < rank; ++q) acc += Up[i * rank + q] * s_t[q];
-        R[i] = fma(s_theta, R[i], (T)acc);
+        if constexpr (DF) {
+          const float2 a = R2[i];
+          const dfv v = df_add(df_mul({a.x, a.y}, df_from_double(s_theta)), {acc, 0.f});
+          R2[i] = make_float2(v.hi, v.lo);
+        } else {
+          R[i] = fma(s_theta, R[i], (T)acc);
+        }
       }
       __syncthreads();
     }
     // ---- scatter: u += omega d / abar ----
-    const T scale = corr ? om / s_abar : om * s_theta / s_abar;
+    const T scale = s_scale;
     for (int t = threadIdx.x; t < NINT; t += NT) {
       const int x = t % M, y = (t / M) % M, z = DIM == 3 ? t / (M * M) : 0;
       const long long gi = origin + 1 + x + py * (y + 1) + (DIM == 3 ? pz * (z + 1) : 0);
-      u[gi] = fma(scale, R[t], u[gi]);
+      if constexpr (DF) {
+        const float2 a = R2[t];
+        u[gi] = fma(scale, df_to_double({a.x, a.y}), u[gi]);
+      } else {
+        u[gi] = fma(scale, R[t], u[gi]);
+      }
     }
     if (TMA) async::fence_proxy_async();  // slot reads before the next TMA writes into it
     __syncthreads();

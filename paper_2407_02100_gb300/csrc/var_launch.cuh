@@ -51,7 +51,7 @@ static int var_grid(int n_patches) {
 }
 
 template <int DIM, int K>
-static int patch_var_impl(const PatchLaunch& pl, T* u, const T* b, const T* coef, const T* dinv,
+static int patch_var_impl(const PatchLaunch& pl, T* u, const T* b, const T* coef, const T* vscale, const T* dinv,
                           const float* corr, int rank, cudaStream_t s) {
   if (pl.n_patches <= 0) return GMG_OK;
   int* const flag = device_wait_flag();
@@ -65,13 +65,13 @@ static int patch_var_impl(const PatchLaunch& pl, T* u, const T* b, const T* coef
       return GMG_ERR_CUDA;
     const int grid = var_grid<DIM, K, true>(pl.n_patches);
     if (grid <= 0) return GMG_ERR_CUDA;
-    patch_var_kernel<DIM, K, kVarThreads, true><<<grid, kVarThreads, 0, s>>>(u, b, coef, dinv, corr, rank, pl,
-                                                                             maps, flag);
+    patch_var_kernel<DIM, K, kVarThreads, true><<<grid, kVarThreads, 0, s>>>(u, b, coef, vscale, dinv, corr, rank,
+                                                                             pl, maps, flag);
   } else {
     const int grid = var_grid<DIM, K, false>(pl.n_patches);
     if (grid <= 0) return GMG_ERR_CUDA;
-    patch_var_kernel<DIM, K, kVarThreads, false><<<grid, kVarThreads, 0, s>>>(u, b, coef, dinv, corr, rank, pl,
-                                                                              TmaMaps<0>(), flag);
+    patch_var_kernel<DIM, K, kVarThreads, false><<<grid, kVarThreads, 0, s>>>(u, b, coef, vscale, dinv, corr, rank,
+                                                                              pl, TmaMaps<0>(), flag);
   }
   count_launch();
   return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
@@ -101,6 +101,29 @@ int upload_var_tables<GMG_T>(int k, const double* Mc, const double* Kc, const do
   cudaError_t e = cudaMemcpyToSymbol(c_Mc, mc.data(), mc.size() * sizeof(T), off_cell(k) * sizeof(T));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_Kc, kc.data(), kc.size() * sizeof(T), off_cell(k) * sizeof(T));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_T, tt.data(), tt.size() * sizeof(T), off_t(k) * sizeof(T));
+  if (sizeof(T) == 8) {  // float pairs (hi, lo) for the double-float kernels
+    auto split = [](const double* v, int n, std::vector<float>& hi, std::vector<float>& lo) {
+      hi.resize(n);
+      lo.resize(n);
+      for (int i = 0; i < n; ++i) {
+        hi[i] = (float)v[i];
+        lo[i] = (float)(v[i] - (double)hi[i]);
+      }
+    };
+    std::vector<float> h, l;
+    const int nc = (k + 1) * (k + 1);
+    const size_t co = off_cell(k) * sizeof(float), cb = nc * sizeof(float);
+    split(Mc, nc, h, l);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_Mchi, h.data(), cb, co);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_Mclo, l.data(), cb, co);
+    split(Kc, nc, h, l);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_Kchi, h.data(), cb, co);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_Kclo, l.data(), cb, co);
+    split(That, M * M, h, l);
+    const size_t to = off_t(k) * sizeof(float), tb = M * M * sizeof(float);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_Thi, h.data(), tb, to);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_Tlo, l.data(), tb, to);
+  }
   return e == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
 }
 
@@ -113,8 +136,8 @@ int launch_apply_var<GMG_T>(const LevelGeom& g, long long n_elems, const GMG_T* 
 
 template <>
 int launch_patch_var<GMG_T>(const PatchLaunch& pl, GMG_T* u, const GMG_T* b, const GMG_T* coef,
-                            const GMG_T* dinv, const float* corr, int rank, cudaStream_t s) {
-  GMG_VAR_DISPATCH(GMG_NS::patch_var_impl, pl.g.dim, pl.g.k, pl, u, b, coef, dinv, corr, rank, s)
+                            const GMG_T* vscale, const GMG_T* dinv, const float* corr, int rank, cudaStream_t s) {
+  GMG_VAR_DISPATCH(GMG_NS::patch_var_impl, pl.g.dim, pl.g.k, pl, u, b, coef, vscale, dinv, corr, rank, s)
 }
 
 }  // namespace gmg
