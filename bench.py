@@ -547,21 +547,26 @@ def run_ours(args):
     return 0
 
 
-def timed_solve(gmg, torch, P, u, b, local, max_it=300):
-    """One warm-up solve, then one timed solve (CUDA events on the current
-    stream, clocks sampled around it); returns (ms, stats, status, clocks)."""
+def timed_solve(gmg, torch, P, u, b, local, max_it=300, repeats=3):
+    """One warm-up solve, then `repeats` timed solves (CUDA events on the
+    current stream, clocks sampled around them); returns (median ms, stats,
+    status, clocks) of the last solve.  The median keeps one solve slowed by
+    the host (a launch gap) from standing for the leg."""
     u.zero_()
     gmg.cg_gmg_solve(P.h, u, b, RTOL, max_it, raise_on_error=False)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream()
+    times = []
     with ClockSampler(local) as ck:
-        u.zero_()
-        e0.record(stream)
-        status, st = gmg.cg_gmg_solve(P.h, u, b, RTOL, max_it, raise_on_error=False)
-        e1.record(stream)
-        torch.cuda.synchronize()
-    return e0.elapsed_time(e1), st, status, ck.summary()
+        for _ in range(repeats):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            u.zero_()
+            e0.record(stream)
+            status, st = gmg.cg_gmg_solve(P.h, u, b, RTOL, max_it, raise_on_error=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    return sorted(times)[len(times) // 2], st, status, ck.summary()
 
 
 def rel_diff(torch, a, b):

@@ -29,6 +29,8 @@ def main():
     ap.add_argument("--omegas", default="1.0,0.8,0.6")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--fd-only", action="store_true",
+                    help="only the damped-FD solves (no training), with per-phase times")
     a = ap.parse_args()
     build.build()
     prec = gmg.GMG_FP32 if a.precision == "fp32" else gmg.GMG_FP64
@@ -45,12 +47,13 @@ def main():
     nf = max(0, min(nfine, a.samples - (total - nfine)))
     verts = rng.permutation(np.concatenate([rng.permutation(nfine)[:nf], np.arange(nfine, total)]))
     ns = len(verts)
-    res = torch.tensor(np.random.default_rng(a.seed + 3).standard_normal((ns, nint)), device="cuda")
+    res = None if a.fd_only else torch.tensor(np.random.default_rng(a.seed + 3).standard_normal((ns, nint)),
+                                              device="cuda")
     out = {"dim": dim, "degree": k, "n_cells": n, "sigma": a.sigma, "corr_len": a.corr,
            "coef_contrast": float(coef.max() / coef.min()), "samples": ns, "precision": a.precision,
            "runs": []}
     for om in [float(x) for x in a.omegas.split(",")]:
-        for mode in ("fd_mean", "learned"):
+        for mode in ("fd_mean",) if a.fd_only else ("fd_mean", "learned"):
             P = gmg.Problem(dim, k, n, precision=prec, damping=om)
             gmg.gmg_set_coefficient(P.h, coef)
             rec = {"omega": om, "local_solver": mode}
@@ -61,7 +64,7 @@ def main():
                                                    seed=a.seed)
                 torch.cuda.synchronize()
                 rec.update({"train_s": time.perf_counter() - t0, "loss_first": hist[0], "loss_last": hist[-1],
-                            "kept_patches": kept})
+                            "kept_patches": kept, "levels_kept_mask": gmg.gmg_learned_levels(P.h)})
             b = P.to_device(rhs, dtype=torch.float64)
             u = P.zeros(dtype=torch.float64)
             st, s = gmg.cg_gmg_solve(P.h, u, b, 1e-10, 300, raise_on_error=False)
@@ -73,6 +76,11 @@ def main():
             rec.update({"status": gmg.STATUS.get(st, st), "iterations": s.iterations,
                         "rel_residual": s.relative_residual,
                         "time_to_solution_ms": (time.perf_counter() - t0) * 1e3})
+            if a.fd_only:  # a third solve with per-phase GPU times
+                gmg.gmg_set_phase_timing(P.h, True)
+                u.zero_()
+                _, s = gmg.cg_gmg_solve(P.h, u, b, 1e-10, 300, raise_on_error=False)
+                rec["phase_ms"] = gmg.phase_times(s)
             out["runs"].append(rec)
             del P
     print(json.dumps(out))
