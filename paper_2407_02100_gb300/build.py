@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgmg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "patch_f64.cu", "patch_f32.cu", "vector_kernels.cu", "noalloc.cu", "batch.cu", "var_f64.cu", "var_f32.cu", "learned.cu", "patch_tc.cu", "peak.cu", "setup.cpp"]
+SOURCES = ["api.cu", "patch_f64.cu", "patch_f32.cu", "vector_kernels.cu", "transfer_df.cu", "noalloc.cu", "batch.cu", "var_f64.cu", "var_f32.cu", "learned.cu", "patch_tc.cu", "peak.cu", "setup.cpp"]
 
 
 def _nvcc():

@@ -469,7 +469,10 @@ int prolongate_add(gmg_problem* p, int cl, const void* coarse, void* fine) {
     Arr out = last ? level_arr(gf) : compact_arr(ext[0], ext[1], ext[2]);
     void* dst = last ? fine : (a % 2 == 0 ? p->tmp1 : p->tmp2);
     AxisOp op = make_op(a, cur, zero, out, ext, zero, 2 * k, k, 0, k + 1, last ? 1 : 0);
-    CHECK(axis_op(p, op, src, dst, p->coef_prol));
+    if (p->xfer_df)  // FP64 problems: double-float passes, float pairs in between
+      CHECK(launch_transfer_df(op, k, gc.n, false, p->prol_h.data(), src, a > 0, dst, !last, p->stream));
+    else
+      CHECK(axis_op(p, op, src, dst, p->coef_prol));
     cur = out;
     src = dst;
   }
@@ -503,7 +506,10 @@ int restrict_to(gmg_problem* p, int fl, const void* fine, void* coarse) {
     // coarse node c = o + 1 gathers fine nodes 2k(c/k) - (2k-1) .. + (2k-1)
     AxisOp op = make_op(a, cur, ioff, out, cnt, ooff, k, 2 * k, -(2 * k - 1), 4 * k - 1, 0);
     op.shift = 1;
-    CHECK(axis_op(p, op, src, dst, p->coef_rest));
+    if (p->xfer_df)
+      CHECK(launch_transfer_df(op, k, gc.n, true, p->rest_h.data(), src, a > 0, dst, !last, p->stream));
+    else
+      CHECK(axis_op(p, op, src, dst, p->coef_rest));
     cur = out;
     src = dst;
     ext[a] = Nc;
@@ -741,6 +747,10 @@ int gmg::detail::create_problem(const gmg_desc* d, gmg_problem* p, const CreateO
       rest[q * W + w] = v;
     }
   CHECK(upload_table(p, &p->coef_rest, rest));
+  p->prol_h = prol;
+  p->rest_h = rest;
+  p->xfer_df = p->esize == 8 && transfer_table_df_ok(k, false, prol.data()) &&
+               transfer_table_df_ok(k, true, rest.data());
   // transfer temporaries: largest intermediate array of any pass
   long long tmax = 1;
   for (int l = 1; l < L; ++l) {

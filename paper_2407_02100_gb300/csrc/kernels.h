@@ -162,6 +162,16 @@ int launch_dense_solve(const LevelGeom& g, const double* Ainv, int n_int, const 
 
 template <typename T>
 int launch_axis_op(const AxisOp& op, const T* in, T* out, const T* coef, cudaStream_t s);
+// The transfer passes of FP64 problems in double-float arithmetic
+// (transfer_df.cu): op is the prolongation (restrict_op false) or
+// restriction pass that launch_axis_op would run, table its coefficient
+// table (host FP64, rows of op.W), n_cells the coarse cells along the pass
+// axis; in / out are doubles, or float pairs where in_df / out_df.
+// transfer_table_df_ok checks that a table has the zero pattern the kernel
+// relies on.
+int transfer_table_df_ok(int k, bool restrict_op, const double* table);
+int launch_transfer_df(const AxisOp& op, int k, int n_cells, bool restrict_op, const double* table,
+                       const void* in, bool in_df, void* out, bool out_df, cudaStream_t s);
 template <typename T>
 int launch_scale(long long n, T* x, const T* d, cudaStream_t s);  // x *= d
 // element-type conversions over n elements

@@ -55,6 +55,10 @@ struct gmg_problem {
   // restriction k x (4k-1)
   void* coef_prol = nullptr;
   void* coef_rest = nullptr;
+  // host copies of the transfer tables, read by the double-float transfer
+  // passes of FP64 problems (xfer_df: the tables have the expected pattern)
+  std::vector<double> prol_h, rest_h;
+  bool xfer_df = false;
   void* tmp1 = nullptr;  // transfer temporaries
   void* tmp2 = nullptr;
   // coarsest-level fast diagonalisation

@@ -97,7 +97,11 @@ def test_damped_sweep(gmg, omega):
     close(P.from_device(ud), s.sweep(u0, b), what="damped sweep")
 
 
-TRANSFER_CASES = [(2, 1, 8), (2, 2, 6), (2, 3, 4), (2, 5, 4), (3, 1, 6), (3, 2, 4), (3, 3, 4), (3, 4, 2)]
+# FP64 problems run the transfers in double-float arithmetic (one coarse
+# cell of outputs per thread): the cases span several coarse cells per axis,
+# degrees up to 8 and both dimensions
+TRANSFER_CASES = [(2, 1, 8), (2, 2, 6), (2, 3, 4), (2, 5, 4), (2, 8, 4), (3, 1, 6), (3, 2, 4), (3, 3, 4),
+                  (3, 3, 6), (3, 4, 2), (3, 4, 4), (3, 7, 2), (3, 8, 2)]
 
 
 @pytest.mark.parametrize("dim,k,n", TRANSFER_CASES)
