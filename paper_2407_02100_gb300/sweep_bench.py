@@ -36,8 +36,12 @@ def main():
                     help="FP64 3D: evaluate every patch residual on its own closure (no shared faces)")
     ap.add_argument("--tile-operator", action="store_true",
                     help="FP64 3D: time the tile kernel instead of the three-pass operator")
+    ap.add_argument("--transfers", action="store_true",
+                    help="time the restriction to and prolongation from the next coarser level instead")
     a = ap.parse_args()
     build.build()
+    if a.transfers:
+        return time_transfers(a)
     prec = {"fp64": gmg.GMG_FP64, "fp32": gmg.GMG_FP32, "fp32_tc": gmg.GMG_FP32_TC,
             "fp32_tf32": gmg.GMG_FP32_TF32}[a.precision]
     P = gmg.Problem(a.dim, a.degree, a.n, n_levels=1, precision=prec)
@@ -71,6 +75,33 @@ def main():
                       "three_pass_operator": gmg.gmg_three_pass_operator(P.h),
                       "nodes": nodes, "sweep_ms": t_sweep * 1e3, "sweep_mdofs": nodes / t_sweep / 1e6,
                       "apply_ms": t_apply * 1e3, "apply_mdofs": nodes / t_apply / 1e6}))
+    P.close()
+
+
+def time_transfers(a):
+    """Restriction of a fine-level vector to the next coarser level and
+    prolongation back (added to the fine vector), timed over a.sweeps calls
+    each after a.warmup."""
+    prec = {"fp64": gmg.GMG_FP64, "fp32": gmg.GMG_FP32}[a.precision]
+    P = gmg.Problem(a.dim, a.degree, a.n, n_levels=2, precision=prec)
+    f = P.to_device(inputs.random_nodal(a.dim, a.degree, a.n, 1))
+    c = P.zeros(0)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    for _ in range(a.warmup):
+        gmg.gmg_restrict(P.h, 1, f, c)
+        gmg.gmg_prolongate_add(P.h, 0, c, f)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.sweeps):
+        gmg.gmg_restrict(P.h, 1, f, c)
+    e1.record()
+    for _ in range(a.sweeps):
+        gmg.gmg_prolongate_add(P.h, 0, c, f)
+    e2.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"dim": a.dim, "degree": a.degree, "n_cells": a.n, "precision": a.precision,
+                      "restrict_ms": e0.elapsed_time(e1) / a.sweeps,
+                      "prolongate_ms": e1.elapsed_time(e2) / a.sweeps}))
     P.close()
 
 
