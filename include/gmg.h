@@ -480,6 +480,25 @@ int gmg_slab_width(const gmg_problem* p, int level);
 int gmg_set_shared_faces(gmg_problem* p, int enable);
 int gmg_shared_faces(const gmg_problem* p);
 
+/* ---- Coarse-level sweep of FP64 problems -----------------------------------
+ * A whole-colour sweep step (Algorithm 4) of an FP64 problem whose colour
+ * holds at most max_patches patches runs on the coarse-level kernel: one CTA
+ * per patch and one thread per output of each stage (the residual on the
+ * patch closure by sum factorisation, each fast-diagonalisation transform,
+ * then u += omega d), in double-float arithmetic.  A colour step of a
+ * coarse level lasts as long as one patch takes; the line kernels give a
+ * thread a whole line per stage, this kernel a single output.  Same method
+ * and colour order; results agree with the other forms up to rounding.
+ * Levels swept by it take no slab schedule.
+ * gmg_set_small_sweep: max_patches >= 0 (0 turns the kernel off; gmg_create
+ *   sets 256 for degrees up to 4 and 0 above); GMG_ERR_INVALID_ARG for a
+ *   null problem or a negative count.  Single-precision and variable-
+ *   coefficient problems ignore it.
+ * gmg_small_sweep: the current max_patches, GMG_ERR_INVALID_ARG for a null
+ *   problem. */
+int gmg_set_small_sweep(gmg_problem* p, int max_patches);
+int gmg_small_sweep(const gmg_problem* p);
+
 /* ---- Three-pass FP64 operator -------------------------------------------
  * In 3D at degree >= 3 the FP64 level operator (the stiffness operator of
  * Sec. 2, evaluated matrix-free by sum factorisation as in App. A.1;

@@ -204,6 +204,10 @@ PatchLaunch colour_launch(const Level& L, int colour, double omega) {
 int launch_colour(gmg_problem* p, const PatchLaunch& pl, void* u, const void* b) {
   if (pl.n_patches == 0) return GMG_OK;
   if (p->esize == 8) {
+    if (pl.n_patches <= p->small_patches) {  // a coarse level: one output per thread
+      const int st = launch_patch_small<double>(pl, (double*)u, (const double*)b, (const double*)p->dinv, p->stream);
+      if (st != GMG_ERR_UNSUPPORTED) return st;
+    }
     if (p->faces && p->shared_faces) {
       const int st = launch_patch_faces<double>(pl, (double*)u, (const double*)b, (const double*)p->dinv,
                                                 (double*)p->faces, p->stream);
@@ -247,8 +251,21 @@ int smooth_colour(gmg_problem* p, int level, void* u, const void* b, int colour)
 // reads exactly the values Algorithm 4 gives it: the sweep does not depend
 // on W.  Only the working set between consecutive launches changes: about
 // (W + 2) k node planes of u and b.
+// Largest number of patches in one colour of level L.
+long long max_colour_patches(const gmg_problem* p, const Level& L) {
+  long long m = 0;
+  for (int c = 0; c < (1 << L.g.dim); ++c) m = std::max<long long>(m, colour_launch(L, c, p->desc.damping).n_patches);
+  return m;
+}
+
+// FP64 levels whose colours all take the coarse-level kernel (gmg_set_small_sweep)
+bool small_level(const gmg_problem* p, const Level& L) {
+  return p->esize == 8 && !p->varcoef && max_colour_patches(p, L) <= p->small_patches;
+}
+
 int slab_width_for(const gmg_problem* p, const Level& L) {
-  if (p->varcoef || p->slab_width == 0) return 0;
+  // a small FP64 level is swept by the coarse-level kernel, one CTA per patch
+  if (p->varcoef || p->slab_width == 0 || small_level(p, L)) return 0;
   const int nc = 1 << L.g.dim, span = L.g.n - 1 + nc;  // slab index range at W = 1
   int W = p->slab_width;
   if (W < 0) {  // the largest slab whose node planes of u and b fill half of the 126 MB L2
@@ -648,6 +665,10 @@ int gmg::detail::create_problem(const gmg_desc* d, gmg_problem* p, const CreateO
   p->esize = d->precision == GMG_FP64 ? 8 : 4;
   if (!device_wait_flag()) return GMG_ERR_CUDA;  // resolved once, outside any graph capture
   const int dim = d->dim, k = d->degree;
+  // colour steps of up to 256 patches take the one-output-per-thread kernel
+  // at k <= 4, where it measured faster than the line kernels; above, a
+  // patch's outputs outnumber a CTA's threads and it measured slower
+  p->small_patches = k <= 4 ? 256 : 0;
   // level hierarchy: n_levels given, or halve while even and >= 2
   int L = d->n_levels;
   if (L == 0) {
@@ -1119,6 +1140,20 @@ int gmg_set_shared_faces(gmg_problem* p, int enable) {
 int gmg_shared_faces(const gmg_problem* p) {
   if (!p) return GMG_ERR_INVALID_ARG;
   return p->shared_faces && p->faces ? 1 : 0;
+}
+
+int gmg_set_small_sweep(gmg_problem* p, int max_patches) {
+  if (!p || max_patches < 0) return GMG_ERR_INVALID_ARG;
+  drop_cg_graph(p);
+  p->small_patches = max_patches;
+  // levels that leave or join the coarse-level kernel take or drop their slabs
+  for (int l = 0; l < (int)p->levels.size(); ++l) CHECK(build_slabs(p, l, slab_width_for(p, p->levels[l])));
+  return GMG_OK;
+}
+
+int gmg_small_sweep(const gmg_problem* p) {
+  if (!p) return GMG_ERR_INVALID_ARG;
+  return p->small_patches;
 }
 
 int gmg_set_slab_width(gmg_problem* p, int width) {

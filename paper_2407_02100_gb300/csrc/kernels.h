@@ -113,6 +113,10 @@ int upload_patch_tables(int k, const double* Mp, const double* Kp, const double*
                         const double* Mc, const double* Kc, cudaStream_t s);
 template <typename T>
 int launch_patch_colour(const PatchLaunch& pl, T* u, const T* b, const T* dinv, cudaStream_t s);
+// one colour of a coarse level with the one-output-per-thread kernel (FP64 problems,
+// mode 0, no patch list; GMG_ERR_UNSUPPORTED otherwise)
+template <typename T>
+int launch_patch_small(const PatchLaunch& pl, T* u, const T* b, const T* dinv, cudaStream_t s);
 // several problems / slices of one colour in one launch (all of dimension
 // dim and degree k); ppc = 0 picks the default patches per CTA, else one of
 // the tuned variants 1, 2, 4 (3D FP32 only; others use the default)

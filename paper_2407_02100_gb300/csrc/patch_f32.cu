@@ -4,3 +4,4 @@
 #include "patch_kernels.cuh"
 #include "patch_launch.cuh"
 #include "face_kernels.cuh"
+#include "small_kernels.cuh"

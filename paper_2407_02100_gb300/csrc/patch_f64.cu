@@ -4,6 +4,7 @@
 #include "patch_kernels.cuh"
 #include "patch_launch.cuh"
 #include "face_kernels.cuh"
+#include "small_kernels.cuh"
 
 namespace gmg {
 

@@ -106,6 +106,9 @@ struct gmg_problem {
   // (gmg_set_shared_faces)
   void* faces = nullptr;
   bool shared_faces = true;
+  // FP64 colour steps of at most this many patches use the coarse-level
+  // kernel (gmg_set_small_sweep; 0: never; set by gmg_create)
+  int small_patches = 0;
   // workspace of the three-pass FP64 3D operator (four finest-level
   // vectors), null where the tile kernel is used
   void* apply_ws = nullptr;

@@ -35,6 +35,7 @@ EXPORTS = ["gmg_create", "gmg_destroy", "gmg_vector_layout", "gmg_level_info",
            "gmg_set_coefficient", "gmg_set_local_solver", "gmg_learned_train",
            "gmg_learned_corrections", "gmg_mlp_loss_grad", "gmg_tc_status", "gmg_tc_probe",
            "gmg_set_slab_width", "gmg_slab_width", "gmg_set_shared_faces", "gmg_shared_faces",
+           "gmg_set_small_sweep", "gmg_small_sweep",
            "gmg_set_three_pass_operator", "gmg_three_pass_operator", "gmg_exact_patch_solve",
            "gmg_set_phase_timing", "gmg_fma_peak", "gmg_learned_levels", "gmg_learned_set_levels",
            "gmg_set_operator_tile", "gmg_autotune"]
@@ -128,6 +129,8 @@ def lib():
             "gmg_slab_width": [vp, i],
             "gmg_set_shared_faces": [vp, i],
             "gmg_shared_faces": [vp],
+            "gmg_set_small_sweep": [vp, i],
+            "gmg_small_sweep": [vp],
             "gmg_set_three_pass_operator": [vp, i],
             "gmg_three_pass_operator": [vp],
         }
@@ -368,6 +371,19 @@ def gmg_set_shared_faces(h, enable):
     _check("gmg_set_shared_faces", lib().gmg_set_shared_faces(h, 1 if enable else 0))
 
 
+def gmg_set_small_sweep(h, max_patches):
+    """FP64 colour steps of at most max_patches patches use the coarse-level
+    kernel, one output per thread (0: never)."""
+    _check("gmg_set_small_sweep", lib().gmg_set_small_sweep(h, int(max_patches)))
+
+
+def gmg_small_sweep(h):
+    v = lib().gmg_small_sweep(h)
+    if v < 0:
+        _check("gmg_small_sweep", v)
+    return v
+
+
 def gmg_shared_faces(h):
     """1 if whole-colour FP64 3D sweeps of the problem use the shared-face form."""
     r = lib().gmg_shared_faces(h)
@@ -421,7 +437,7 @@ class Problem:
     (n k + 1)^dim node arrays (x index fastest) used by the tests."""
 
     def __init__(self, dim, degree, n_cells, n_levels=0, precision=GMG_FP64, damping=1.0,
-                 pre_sweeps=1, post_sweeps=1, stream=None):
+                 pre_sweeps=1, post_sweeps=1, stream=None, small_sweep=None):
         import torch
         self.torch = torch
         self.dim, self.degree, self.n_cells = dim, degree, n_cells
@@ -430,6 +446,8 @@ class Problem:
         self.h = gmg_create(dim, degree, n_cells, n_levels, precision, damping, pre_sweeps,
                             post_sweeps, stream)
         self.n_levels = gmg_level_info(self.h, 0)[1]
+        if small_sweep is not None:  # 0: no colour step takes the coarse-level kernel
+            gmg_set_small_sweep(self.h, small_sweep)
 
     def close(self):
         if self.h is not None:

@@ -36,6 +36,8 @@ def main():
                     help="FP64 3D: evaluate every patch residual on its own closure (no shared faces)")
     ap.add_argument("--tile-operator", action="store_true",
                     help="FP64 3D: time the tile kernel instead of the three-pass operator")
+    ap.add_argument("--graph", action="store_true",
+                    help="capture one sweep (one operator application) as a CUDA graph and time its replays")
     ap.add_argument("--transfers", action="store_true",
                     help="time the restriction to and prolongation from the next coarser level instead")
     a = ap.parse_args()
@@ -44,7 +46,11 @@ def main():
         return time_transfers(a)
     prec = {"fp64": gmg.GMG_FP64, "fp32": gmg.GMG_FP32, "fp32_tc": gmg.GMG_FP32_TC,
             "fp32_tf32": gmg.GMG_FP32_TF32}[a.precision]
-    P = gmg.Problem(a.dim, a.degree, a.n, n_levels=1, precision=prec)
+    # a side stream of our own: graph capture needs one (the legacy default
+    # stream cannot be captured)
+    side = torch.cuda.Stream() if a.graph else torch.cuda.current_stream()
+    with torch.cuda.stream(side):
+        P = gmg.Problem(a.dim, a.degree, a.n, n_levels=1, precision=prec)
     gmg.gmg_set_slab_width(P.h, a.slab)
     gmg.gmg_set_shared_faces(P.h, not a.closure)
     gmg.gmg_set_three_pass_operator(P.h, not a.tile_operator)
@@ -54,14 +60,24 @@ def main():
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def timed(fn, reps):
-        for _ in range(a.warmup):
-            fn()
-        torch.cuda.synchronize()
-        e0.record()
-        for _ in range(reps):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
+        with torch.cuda.stream(side):
+            for _ in range(a.warmup):
+                fn()
+            torch.cuda.synchronize()
+            if a.graph:  # replay one captured call; the launches then cost what they cost in a solve
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=side):
+                    fn()
+                g.replay()
+                torch.cuda.synchronize()
+                run = g.replay
+            else:
+                run = fn
+            e0.record(side)
+            for _ in range(reps):
+                run()
+            e1.record(side)
+            torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps * 1e-3
 
     variant = {"combined": gmg.GMG_SWEEP_COMBINED, "separated": gmg.GMG_SWEEP_SEPARATED,
@@ -73,7 +89,7 @@ def main():
                       "variant": a.variant, "batch": a.batch if a.variant == "batched" else None,
                       "slab_width": gmg.gmg_slab_width(P.h, 0), "shared_faces": gmg.gmg_shared_faces(P.h),
                       "three_pass_operator": gmg.gmg_three_pass_operator(P.h),
-                      "nodes": nodes, "sweep_ms": t_sweep * 1e3, "sweep_mdofs": nodes / t_sweep / 1e6,
+                      "graph": a.graph, "nodes": nodes, "sweep_ms": t_sweep * 1e3, "sweep_mdofs": nodes / t_sweep / 1e6,
                       "apply_ms": t_apply * 1e3, "apply_mdofs": nodes / t_apply / 1e6}))
     P.close()
 

@@ -43,6 +43,7 @@ def test_batch_sweep_equals_single_problems(gmg, dim, k, ns):
         # same form of the single-problem sweep (the shared-face form of FP64
         # 3D problems rounds differently)
         gmg.gmg_set_shared_faces(P.h, False)
+        gmg.gmg_set_small_sweep(P.h, 0)  # nor the coarse-level kernel
         ud = P.to_device(us[i])
         gmg.gmg_smooth(P.h, P.finest, ud, P.to_device(bs[i]), 1, False)
         assert np.array_equal(got[i], P.from_device(ud)), i

@@ -57,7 +57,7 @@ FACE_CASES = [(3, 4), (3, 5), (3, 6), (4, 3), (4, 4), (5, 3), (6, 2), (7, 3), (8
 def test_each_colour_matches_oracle(gmg, k, n):
     m = Mesh(3, k, n)
     s = PatchSmoother(m)
-    P = gmg.Problem(3, k, n, n_levels=1)
+    P = gmg.Problem(3, k, n, n_levels=1, small_sweep=0)  # these sizes would take the coarse-level kernel
     assert gmg.gmg_shared_faces(P.h) == 1
     u0 = inputs.random_nodal(3, k, n, 7101)
     b = inputs.random_nodal(3, k, n, 7102)
@@ -76,7 +76,7 @@ def test_each_colour_matches_oracle(gmg, k, n):
 def test_face_and_closure_forms_agree(gmg, k, n, omega, reverse):
     """Two sweeps with each form from the same state: equal up to rounding,
     and equal to the oracle's (damped) sweeps."""
-    P = gmg.Problem(3, k, n, n_levels=1, damping=omega)
+    P = gmg.Problem(3, k, n, n_levels=1, damping=omega, small_sweep=0)
     u0 = inputs.random_nodal(3, k, n, 7201)
     b = inputs.random_nodal(3, k, n, 7202)
     bd = P.to_device(b)
@@ -99,7 +99,7 @@ def test_unaligned_rhs_takes_the_closure_form(gmg):
     its element-wise gather, bit-identical to that kernel run directly."""
     import torch
     k, n = 4, 5
-    P = gmg.Problem(3, k, n, n_levels=1)
+    P = gmg.Problem(3, k, n, n_levels=1, small_sweep=0)
     u0 = inputs.random_nodal(3, k, n, 7301)
     b = inputs.random_nodal(3, k, n, 7302)
     bb = P.to_device(b)

@@ -55,11 +55,15 @@ SWEEP_CASES = [(2, 1, 9), (2, 2, 32), (2, 3, 11), (2, 4, 6), (2, 6, 5), (2, 8, 4
                (3, 1, 9), (3, 2, 7), (3, 3, 6), (3, 4, 5), (3, 5, 4), (3, 6, 3), (3, 8, 3)]
 
 
+# FP64 colour steps of up to max_patches patches run on the coarse-level kernel
+# (one output per thread); small=1024 takes it for every colour of these
+# meshes, small=0 the closure / shared-face kernels
 @pytest.mark.parametrize("dim,k,n", SWEEP_CASES)
-def test_each_colour_step(gmg, dim, k, n):
+@pytest.mark.parametrize("small", [1024, 0])
+def test_each_colour_step(gmg, dim, k, n, small):
     m = Mesh(dim, k, n)
     s = PatchSmoother(m)
-    P = gmg.Problem(dim, k, n, n_levels=1)
+    P = gmg.Problem(dim, k, n, n_levels=1, small_sweep=small)
     u0 = inputs.random_nodal(dim, k, n, 201)
     b = inputs.random_nodal(dim, k, n, 202)
     bd = P.to_device(b)
@@ -72,10 +76,11 @@ def test_each_colour_step(gmg, dim, k, n):
 
 @pytest.mark.parametrize("dim,k,n", SWEEP_CASES)
 @pytest.mark.parametrize("reverse", [False, True])
-def test_full_sweep(gmg, dim, k, n, reverse):
+@pytest.mark.parametrize("small", [1024, 0])
+def test_full_sweep(gmg, dim, k, n, reverse, small):
     m = Mesh(dim, k, n)
     s = PatchSmoother(m)
-    P = gmg.Problem(dim, k, n, n_levels=1)
+    P = gmg.Problem(dim, k, n, n_levels=1, small_sweep=small)
     u0 = inputs.random_nodal(dim, k, n, 301)
     b = inputs.random_nodal(dim, k, n, 302)
     ud = P.to_device(u0)
@@ -85,11 +90,12 @@ def test_full_sweep(gmg, dim, k, n, reverse):
 
 
 @pytest.mark.parametrize("omega", [0.7, 1.3])
-def test_damped_sweep(gmg, omega):
+@pytest.mark.parametrize("small", [1024, 0])
+def test_damped_sweep(gmg, omega, small):
     dim, k, n = 3, 2, 6
     m = Mesh(dim, k, n)
     s = PatchSmoother(m, omega)
-    P = gmg.Problem(dim, k, n, n_levels=1, damping=omega)
+    P = gmg.Problem(dim, k, n, n_levels=1, damping=omega, small_sweep=small)
     u0 = inputs.random_nodal(dim, k, n, 401)
     b = inputs.random_nodal(dim, k, n, 402)
     ud = P.to_device(u0)
@@ -169,7 +175,7 @@ def test_tma_and_elementwise_gathers_agree(gmg, dim, k, n, prec):
     arithmetic, so the results must be bit-identical, and equal to the
     oracle's sweep to the precision's bound."""
     import torch
-    P = gmg.Problem(dim, k, n, n_levels=1, precision=prec)
+    P = gmg.Problem(dim, k, n, n_levels=1, precision=prec, small_sweep=0)
     u0 = inputs.random_nodal(dim, k, n, 5001)
     b = inputs.random_nodal(dim, k, n, 5002)
     ua = P.to_device(u0)
@@ -190,9 +196,10 @@ def test_tma_and_elementwise_gathers_agree(gmg, dim, k, n, prec):
 # the last colour and empty launches for every other colour
 @pytest.mark.parametrize("dim,k,n", [(2, 3, 2), (3, 2, 2), (3, 4, 2)])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_single_patch_mesh(gmg, dim, k, n, prec):
+@pytest.mark.parametrize("small", [1024, 0])
+def test_single_patch_mesh(gmg, dim, k, n, prec, small):
     m = Mesh(dim, k, n)
-    P = gmg.Problem(dim, k, n, n_levels=1, precision=prec)
+    P = gmg.Problem(dim, k, n, n_levels=1, precision=prec, small_sweep=small)
     u0 = inputs.random_nodal(dim, k, n, 5201)
     b = inputs.random_nodal(dim, k, n, 5202)
     ud = P.to_device(u0)

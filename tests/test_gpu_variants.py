@@ -58,8 +58,10 @@ def test_batched_sweep(gmg, dim, k, n, n_b):
 
 def test_batched_with_whole_colours_is_algorithm4_bitwise(gmg):
     dim, k, n = 3, 3, 8
-    P = gmg.Problem(dim, k, n, n_levels=1)
-    gmg.gmg_set_shared_faces(P.h, False)  # Algorithm 5 batches use the closure form
+    # Algorithm 5 batches use the closure form: so must the reference sweep
+    # (no shared faces, no coarse-level kernel)
+    P = gmg.Problem(dim, k, n, n_levels=1, small_sweep=0)
+    gmg.gmg_set_shared_faces(P.h, False)
     u0 = inputs.random_nodal(dim, k, n, 1601)
     bd = P.to_device(inputs.random_nodal(dim, k, n, 1602))
     a, c = P.to_device(u0), P.to_device(u0)
