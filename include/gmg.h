@@ -178,11 +178,17 @@ int gmg_smooth_variant(gmg_problem* p, int level, void* u, const void* b, int va
 
 /* coarse = R fine with R = P^T, the transpose of the embedding prolongation
  * (Sec. 2, restriction as the adjoint of the embedding).  fine: level
- * `fine_level` (>= 1), coarse: level fine_level-1; problem's vector type. */
+ * `fine_level` (>= 1), coarse: level fine_level-1; problem's vector type.
+ * One pass per axis; FP64 problems compute the passes in double-float
+ * arithmetic (agreeing with FP64 arithmetic to about 1e-14 relative) and
+ * use the problem's two transfer temporaries, so calls on one problem must
+ * not overlap.  Errors: INVALID_ARG (level out of range, null vector),
+ * UNSUPPORTED (a pass too large for one launch), CUDA. */
 int gmg_restrict(gmg_problem* p, int fine_level, const void* fine, void* coarse);
 
 /* fine += P coarse, P the embedding of V_{l} into V_{l+1} (Sec. 2).
- * coarse: level `coarse_level`, fine: level coarse_level+1. */
+ * coarse: level `coarse_level`, fine: level coarse_level+1.  Passes,
+ * arithmetic, temporaries and errors as for gmg_restrict. */
 int gmg_prolongate_add(gmg_problem* p, int coarse_level, const void* coarse, void* fine);
 
 /* x = A_0^{-1} b on the coarsest level, by fast diagonalisation of the
