@@ -34,11 +34,11 @@ struct WideSmem {
   static constexpr int ITEMS = DIM == 3 ? C * C * M : C * M;
 };
 
-// threads per CTA: the largest stage in two passes (up to 1024 threads)
-template <int DIM, int K>
+// threads per CTA: the largest stage in PASSES passes (128 to 1024 threads)
+template <int DIM, int K, int PASSES>
 constexpr int wide_threads() {
   constexpr int items = WideSmem<DIM, K>::ITEMS;
-  constexpr int t = (items + 1) / 2;
+  constexpr int t = (items + PASSES - 1) / PASSES;
   return t <= 128 ? 128 : t >= 1024 ? 1024 : (t + 31) / 32 * 32;
 }
 
@@ -201,25 +201,32 @@ __global__ void __launch_bounds__(NT) patch_wide_df_kernel(const PatchLaunch pl,
   }
 }
 
+template <int DIM, int K, int NT>
+static int wide_launch(const PatchLaunch& pl, T* u, const T* b, const T* dinv, cudaStream_t s) {
+  using Z = WideSmem<DIM, K>;
+  auto kern = patch_wide_df_kernel<DIM, K, NT>;
+  static PerDevice<bool> ready_dev;
+  bool* const ready = ready_dev.get();
+  if (!ready) return GMG_ERR_CUDA;
+  if (!*ready) {
+    if (prepare(kern, Z::BYTES) != GMG_OK) return GMG_ERR_CUDA;
+    *ready = true;
+  }
+  kern<<<pl.n_patches, NT, Z::BYTES, s>>>(pl, u, b, dinv);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+}
+
 template <int DIM, int K>
 static int wide_impl(const PatchLaunch& pl, T* u, const T* b, const T* dinv, cudaStream_t s) {
   if constexpr (sizeof(T) != 8) {
     return GMG_ERR_UNSUPPORTED;
   } else {
     if (pl.n_patches <= 0) return GMG_OK;
-    using Z = WideSmem<DIM, K>;
-    constexpr int NT = wide_threads<DIM, K>();
-    auto kern = patch_wide_df_kernel<DIM, K, NT>;
-    static PerDevice<bool> ready_dev;
-    bool* const ready = ready_dev.get();
-    if (!ready) return GMG_ERR_CUDA;
-    if (!*ready) {
-      if (prepare(kern, Z::BYTES) != GMG_OK) return GMG_ERR_CUDA;
-      *ready = true;
-    }
-    kern<<<pl.n_patches, NT, Z::BYTES, s>>>(pl, u, b, dinv);
-    count_launch();
-    return cudaGetLastError() == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+    // fewer patches than SMs: each CTA has an SM to itself, so give it the
+    // largest stage in one pass; otherwise two passes, for more resident CTAs
+    if (pl.n_patches <= sm_count()) return wide_launch<DIM, K, wide_threads<DIM, K, 1>()>(pl, u, b, dinv, s);
+    return wide_launch<DIM, K, wide_threads<DIM, K, 2>()>(pl, u, b, dinv, s);
   }
 }
 
