@@ -33,6 +33,25 @@ def test_prolongation_reproduces_coarse_polynomials(dim, k):
     np.testing.assert_allclose(P @ p(c.node_coordinates()), p(f.node_coordinates()), atol=1e-14)
 
 
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 7, 8])
+def test_restriction_rows_stay_in_their_coarse_cell(k):
+    """The support the transfer kernels rely on, read off the oracle's P:
+    a coarse node c inside coarse cell j (c mod k != 0) restricts only fine
+    nodes strictly inside that cell (2k j < x_f < 2k j + 2k); a coarse
+    vertex c = k j restricts fine nodes within 2k - 1 of its position 2c.
+    Checked along x on a 2D mesh (the y factor only scales the rows)."""
+    c, f = Mesh(2, k, 3), Mesh(2, k, 6)
+    P = prolongation(c, f)
+    fx, cx = f.node_multi()[:, 0], c.node_multi()[:, 0]  # x lattice index of every node
+    nz_f, nz_c = np.nonzero(np.abs(P) > 1e-15)
+    for xf, xc in zip(fx[nz_f], cx[nz_c]):
+        j = xc // k
+        if xc % k:
+            assert 2 * k * j < xf < 2 * k * j + 2 * k, (xc, xf)
+        else:
+            assert abs(xf - 2 * xc) <= 2 * k - 1, (xc, xf)
+
+
 @pytest.mark.parametrize("dim,k,ns", [(2, 1, (4, 8, 16)), (2, 2, (4, 8, 16)), (2, 3, (2, 4, 8)),
                                       (3, 1, (2, 4, 8)), (3, 2, (2, 4))])
 def test_manufactured_solution_converges_at_rate_k_plus_1(dim, k, ns):
