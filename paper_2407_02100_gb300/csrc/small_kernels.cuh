@@ -29,7 +29,12 @@ struct WideSmem {
   // residual and FD work
   static constexpr int X = DIM == 3 ? cmax(C * C * C, 2 * C * M * M) : cmax(C * C, M * M);
   static constexpr int Y = DIM == 3 ? cmax(2 * C * C * M, NINT) : cmax(2 * C * M, NINT);
-  static constexpr int BYTES = (X + Y) * (int)sizeof(float2);
+  // the patch matrices M_p, K_p (M x C) and the eigenvectors T (M x M) as
+  // float pairs, copied from __constant__ memory once per CTA: a stage's
+  // output index varies across the CTA, and shared-memory pairs take one
+  // load where constant memory would take two serialised ones
+  static constexpr int TAB = 2 * M * C + M * M;
+  static constexpr int BYTES = (X + Y + TAB) * (int)sizeof(float2);
   // outputs of the largest stage
   static constexpr int ITEMS = DIM == 3 ? C * C * M : C * M;
 };
@@ -42,42 +47,41 @@ constexpr int wide_threads() {
   return t <= 128 ? 128 : t >= 1024 ? 1024 : (t + 31) / 32 * 32;
 }
 
-// acc += sum over the band of closure row i + 1 of E (KIND 0: M_p, 1: K_p)
-// of E[i][j] x[j * s]: rows left of the patch centre couple to closure
-// columns 0..k, rows right of it to k..2k, the centre row to all 2k + 1
-template <int K, int KIND>
-__device__ __forceinline__ void wide_row(df_acc& acc, int i, const float2* x, int s) {
+// acc += sum over the band of closure row i + 1 of E (M_p or K_p, pairs in
+// shared memory, rows of C) of E[i][j] x[j * s]: rows left of the patch
+// centre couple to closure columns 0..k, rows right of it to k..2k, the
+// centre row to all 2k + 1
+template <int K>
+__device__ __forceinline__ void wide_row(df_acc& acc, int i, const float2* E, const float2* x, int s) {
   constexpr int C = 2 * K + 1;
   const int j0 = i + 1 > K ? K : 0;
-  const int o = off_patch(K) + i * C;
+  const float2* const e = E + i * C;
 #pragma unroll
   for (int q = 0; q <= K; ++q) {
     const int j = j0 + q;
-    const float2 v = x[j * s];
-    df_acc_add(acc, KIND == 0 ? c_Mphi[o + j] : c_Kphi[o + j], KIND == 0 ? c_Mplo[o + j] : c_Kplo[o + j],
-               {v.x, v.y});
+    const float2 v = x[j * s], c = e[j];
+    df_acc_add(acc, c.x, c.y, {v.x, v.y});
   }
   if (i + 1 == K) {  // the centre row also reaches the right cell
 #pragma unroll
     for (int j = K + 1; j < C; ++j) {
-      const float2 v = x[j * s];
-      df_acc_add(acc, KIND == 0 ? c_Mphi[o + j] : c_Kphi[o + j], KIND == 0 ? c_Mplo[o + j] : c_Kplo[o + j],
-                 {v.x, v.y});
+      const float2 v = x[j * s], c = e[j];
+      df_acc_add(acc, c.x, c.y, {v.x, v.y});
     }
   }
 }
 
-// output i of the FD transform of the line x (M values, stride s): forward
-// sum_j T[j][i] x_j, backward sum_j T[i][j] x_j
+// output i of the FD transform of the line x (M values, stride s), T the
+// eigenvector pairs in shared memory: forward sum_j T[j][i] x_j, backward
+// sum_j T[i][j] x_j
 template <int K, bool FORWARD>
-__device__ __forceinline__ dfv wide_fd(int i, const float2* x, int s) {
+__device__ __forceinline__ dfv wide_fd(int i, const float2* T, const float2* x, int s) {
   constexpr int M = 2 * K - 1;
   df_acc acc = {0.f, 0.f};
 #pragma unroll
   for (int j = 0; j < M; ++j) {
-    const int o = off_t(K) + (FORWARD ? j * M + i : i * M + j);
-    const float2 v = x[j * s];
-    df_acc_add(acc, c_Thi[o], c_Tlo[o], {v.x, v.y});
+    const float2 v = x[j * s], c = T[FORWARD ? j * M + i : i * M + j];
+    df_acc_add(acc, c.x, c.y, {v.x, v.y});
   }
   return df_acc_value(acc);
 }
@@ -91,6 +95,9 @@ __global__ void __launch_bounds__(NT) patch_wide_df_kernel(const PatchLaunch pl,
   extern __shared__ __align__(16) float2 wide_smem[];
   float2* const X = wide_smem;
   float2* const Y = wide_smem + Z::X;
+  float2* const Mp = Y + Z::Y;   // M x C pairs
+  float2* const Kp = Mp + M * C;  // M x C pairs
+  float2* const Tt = Kp + M * C;  // M x M pairs
   const float2* const dd = reinterpret_cast<const float2*>(dinv + NINT);  // the diagonal as float pairs
   const long long py = pl.g.py, pz = pl.g.pz;
   const int pid = blockIdx.x;
@@ -99,6 +106,11 @@ __global__ void __launch_bounds__(NT) patch_wide_df_kernel(const PatchLaunch pl,
   const long long origin = (long long)(pl.first[0] + 2 * i0 - 1) * K + py * ((pl.first[1] + 2 * i1 - 1) * K) +
                            (DIM == 3 ? pz * ((pl.first[2] + 2 * i2 - 1) * K) : 0);
   auto st = [](const dfv a) -> float2 { return make_float2(a.hi, a.lo); };
+  for (int t = threadIdx.x; t < M * C; t += NT) {
+    Mp[t] = make_float2(c_Mphi[off_patch(K) + t], c_Mplo[off_patch(K) + t]);
+    Kp[t] = make_float2(c_Kphi[off_patch(K) + t], c_Kplo[off_patch(K) + t]);
+  }
+  for (int t = threadIdx.x; t < M * M; t += NT) Tt[t] = make_float2(c_Thi[off_t(K) + t], c_Tlo[off_t(K) + t]);
   // ---- gather the closure of u as float pairs ([z][y][x]) ----
   for (int t = threadIdx.x; t < (DIM == 3 ? C * C * C : C * C); t += NT) {
     const int x = t % C, y = (t / C) % C, z = DIM == 3 ? t / (C * C) : 0;
@@ -110,8 +122,8 @@ __global__ void __launch_bounds__(NT) patch_wide_df_kernel(const PatchLaunch pl,
     for (int t = threadIdx.x; t < C * C * M; t += NT) {
       const int l = t % (C * C), i = t / (C * C);
       df_acc p = {0.f, 0.f}, q = {0.f, 0.f};
-      wide_row<K, 0>(p, i, X + l, C * C);
-      wide_row<K, 1>(q, i, X + l, C * C);
+      wide_row<K>(p, i, Mp, X + l, C * C);
+      wide_row<K>(q, i, Kp, X + l, C * C);
       Y[l + i * C * C] = st(df_acc_value(p));
       Y[C * C * M + l + i * C * C] = st(df_acc_value(q));
     }
@@ -121,9 +133,9 @@ __global__ void __launch_bounds__(NT) patch_wide_df_kernel(const PatchLaunch pl,
       const int x = t % C, z = (t / C) % M, i = t / (C * M);
       const int src = x + z * C * C;
       df_acc a1 = {0.f, 0.f}, a2 = {0.f, 0.f};
-      wide_row<K, 0>(a1, i, Y + src, C);
-      wide_row<K, 1>(a2, i, Y + src, C);
-      wide_row<K, 0>(a2, i, Y + C * C * M + src, C);
+      wide_row<K>(a1, i, Mp, Y + src, C);
+      wide_row<K>(a2, i, Kp, Y + src, C);
+      wide_row<K>(a2, i, Mp, Y + C * C * M + src, C);
       X[x + i * C + z * C * M] = st(df_acc_value(a1));
       X[C * M * M + x + i * C + z * C * M] = st(df_acc_value(a2));
     }
@@ -133,8 +145,8 @@ __global__ void __launch_bounds__(NT) patch_wide_df_kernel(const PatchLaunch pl,
     for (int t = threadIdx.x; t < C * M; t += NT) {
       const int l = t % C, i = t / C;
       df_acc p = {0.f, 0.f}, q = {0.f, 0.f};
-      wide_row<K, 0>(p, i, X + l, C);
-      wide_row<K, 1>(q, i, X + l, C);
+      wide_row<K>(p, i, Mp, X + l, C);
+      wide_row<K>(q, i, Kp, X + l, C);
       Y[l + i * C] = st(df_acc_value(p));
       Y[C * M + l + i * C] = st(df_acc_value(q));
     }
@@ -152,8 +164,8 @@ __global__ void __launch_bounds__(NT) patch_wide_df_kernel(const PatchLaunch pl,
       const long long row = origin + 1 + py * ((DIM == 3 ? l % M : l) + 1) + (DIM == 3 ? pz * (l / M + 1) : 0);
       const dfv bb = df_mul(df_from_double(b[row + i]), {sbf, 0.f});
       df_acc acc = {0.f, 0.f};
-      wide_row<K, 1>(acc, i, S1 + C * l, 1);
-      wide_row<K, 0>(acc, i, S1 + PLANE + C * l, 1);
+      wide_row<K>(acc, i, Kp, S1 + C * l, 1);
+      wide_row<K>(acc, i, Mp, S1 + PLANE + C * l, 1);
       R[t] = st(df_add(bb, df_neg(df_acc_value(acc))));
     }
   }
@@ -168,7 +180,7 @@ __global__ void __launch_bounds__(NT) patch_wide_df_kernel(const PatchLaunch pl,
       const int i = axis == 0 ? x : axis == 1 ? y : z;                      // output index on the line
       const int s = axis == 0 ? 1 : axis == 1 ? M : M * M;                   // line stride
       const float2* line = A + t - i * s;
-      dfv v = forward ? wide_fd<K, true>(i, line, s) : wide_fd<K, false>(i, line, s);
+      dfv v = forward ? wide_fd<K, true>(i, Tt, line, s) : wide_fd<K, false>(i, Tt, line, s);
       if (scale) {
         const float2 d = __ldg(dd + t);
         v = df_mul(v, {d.x, d.y});
